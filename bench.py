@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the Voronoi point-inclusion test (arXiv 2007.15385) on GB300.
+
+One step = one pip_test over the vehicle-footprint workload: a 12-vertex
+convex footprint (2.4 m x 1.0 m ellipse) against 2^26 float32 lidar-like
+points, packed inclusion bitmask out, bit-exact (float32 filter + exact
+refine).  The metric is point x edge tests per second (full work: every point
+meets every edge).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs the whole workload on its own GPU (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+``--impl reference`` times the CPU oracle (exact predicate, one thread) on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Gtests/s (point×edge) and % of HBM/FP32 roofline; "
+          "Voronoi vs sign-of-offset/ray on GB300")
+UNIT = "Gtests/s"
+WORKLOAD = "vehicle_footprint"
+NUM_POINTS = 1 << 26
+FALLBACK_HBM_GBS = 6800.0
+
+# dram bytes (read + write) per launch of the streaming kernel on this
+# workload, from one ncu capture (profiles/stream_kernel_vehicle_footprint.md),
+# valid only while the kernel sources hash to the value recorded with it.
+NCU_TRAFFIC = {"bytes": None, "sources_sha": None}
+KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_test.cu",
+                  "paper_2007_15385_gb300/csrc/pip_kernels.cuh",
+                  "paper_2007_15385_gb300/csrc/pip_internal.cuh"]
+
+
+def sources_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the GPU works."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_run(w, sample: int) -> dict:
+    """The oracle (exact predicate, one thread) on the first `sample` points."""
+    import oracle
+    pts = np.ascontiguousarray(w.points[:sample])
+    n = int(w.edges()[0])
+    oracle.inside_exact(w.vertices, pts[:1024])  # build + warm
+    t0 = time.perf_counter()
+    oracle.inside_exact(w.vertices, pts)
+    dt = time.perf_counter() - t0
+    return {"value": sample * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d of the %d points, oracle.inside_exact (exact orientation "
+                      "predicate, early exit per point), single thread, %.2f s" % (sample, len(w.points), dt)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed as the reference arm."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2007_15385_gb300 import workloads as wl
+    w = wl.vehicle_footprint(m=NUM_POINTS)
+    import oracle
+    n = int(w.edges()[0])
+    # size each step's sample so that warm-up + timed steps end within ~3 minutes
+    probe = 1 << 16
+    t0 = time.perf_counter()
+    oracle.inside_exact(w.vertices, np.ascontiguousarray(w.points[:probe]))
+    per_point = (time.perf_counter() - t0) / probe
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    sample = int(min(1 << 24, max(1 << 14, budget / per_point)))
+    sample = 1 << int(np.floor(np.log2(sample)))
+    rng = np.random.default_rng(7)
+    starts = rng.integers(0, NUM_POINTS - sample, size=args.steps + args.warmup)
+    times = []
+    for i, s in enumerate(starts):
+        pts = np.ascontiguousarray(w.points[s:s + sample])
+        t0 = time.perf_counter()
+        oracle.inside_exact(w.vertices, pts)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = sample * n * len(times) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "num_points": NUM_POINTS, "edges": n,
+                   "sample_points_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d consecutive points per step at seeded offsets, "
+                                   "oracle.inside_exact, single thread" % sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2007_15385_gb300 import binding as B
+    from paper_2007_15385_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = wl.vehicle_footprint(m=NUM_POINTS)
+    M = w.num_points
+    n = int(w.edges()[0])
+    v = torch.from_numpy(w.vertices).to(dev)
+    vo = torch.from_numpy(w.vertex_offsets).to(dev)
+    p = torch.from_numpy(w.points).to(dev)
+    mask = torch.empty((M + 31) // 32, dtype=torch.int32, device=dev)
+    t = B.pip_prepare(v, vo, max_points=M)
+    st, _ = B.pip_get_status(t)
+    assert st == B.PIP_OK
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        tt = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    # warm-up: W steps, and at least 1 s of them so that clocks settle
+    t_w = time.perf_counter()
+    i = 0
+    while i < args.warmup or time.perf_counter() - t_w < 1.0:
+        B.pip_test(t, p, mask=mask)
+        i += 1
+        if i % 100 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    B.pip_timing(t, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        B.pip_test(t, p, mask=mask)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1))
+    calls, bulk_ms, refine_ms = B.pip_timing_read(t)
+    B.pip_timing(t, False)
+    _, refine_count = B.pip_get_status(t)
+    ms_step = ms_total / args.steps
+    tests_per_step = M * n
+    value = tests_per_step * world / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant (bulk streaming) kernel
+    bytes_per_launch = M * 8 + ((M + 31) // 32) * 4
+    bulk_avg_ms = bulk_ms / max(1, calls)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_launch / (bulk_avg_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources_sha"] == sources_sha() else None
+
+    # end to end through the public API with host buffers
+    p_host = torch.from_numpy(w.points).pin_memory()
+    mask_host = torch.empty_like(mask, device="cpu").pin_memory()
+    for _ in range(3):
+        B.pip_test_host(t, p_host, p, mask, mask_host)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 50))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        B.pip_test_host(t, p_host, p, mask, mask_host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / e2e_steps
+    e2e_value = tests_per_step * world / (e2e_ms * 1e-3) / 1e9
+
+    # same-chip comparators on the same workload (Alg. 2, Alg. 1, plain fp64 Alg. 5)
+    comparators = {}
+    if not args.no_comparators:
+        for name, fn, reps in (("sign_of_offset_f32", B.pip_test_sign_of_offset, 20),
+                               ("ray_crossing_f32", B.pip_test_ray_crossing, 20),
+                               ("voronoi_plain_fp64", B.pip_test_voronoi_fp64, 3)):
+            fn(t, p, mask=mask)
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(reps):
+                fn(t, p, mask=mask)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            cms = c0.elapsed_time(c1) / reps
+            comparators[name] = {"ms": cms, "Gtests_per_s": tests_per_step / (cms * 1e-3) / 1e9}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_run(w, 1 << 25)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "num_points": M, "edges": n,
+                       "polygon": "12 vertices on a 2.4 m x 1.0 m ellipse",
+                       "points": "60% uniform in a 40 m square, 40% in 200 Gaussian clusters (sigma 0.3 m)",
+                       "output": "packed uint32 bitmask, bit-exact (float32 filter + exact refine)",
+                       "l2": "no flush: the 512 MiB of points exceed the 129 MB L2 every step",
+                       "refined_points_per_step": refine_count},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(p_host.numel() * 4),
+                    "d2h_bytes_per_step": int(mask_host.numel() * 4)},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind + " hbm_gbs",
+                         "kernel": "stream_kernel (bulk float32 test)",
+                         "bytes_per_launch": bytes_per_launch, "kernel_ms": bulk_avg_ms,
+                         "refine_kernel_ms": refine_ms / max(1, calls)},
+            "comparators": comparators,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    t.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/*
+ * pip.h -- C ABI of libpip, a GB300 (sm_103a) implementation of the Voronoi
+ * point-inclusion test for convex polygons of Zengin & Sezer,
+ * "A Novel Point Inclusion Test for Convex Polygons Based on Voronoi
+ * Tessellations" (arXiv 2007.15385).
+ *
+ * The method (Sec. 3-4 of the paper): each convex polygon becomes a set of
+ * Voronoi generators -- the centroid p0 (Eq. 3-4, Alg. 3) and its mirror p_k
+ * across every edge line (Eq. 8, Alg. 4) -- and a point x is inside when no
+ * outer generator is nearer than p0 (Eq. 1, Alg. 5).  Squaring (Eq. 10-11)
+ * and expanding turns the test for edge k into the affine sign test
+ *     s_k(x) = t_k - x . w_k >= 0,   w_k = 2 (p_k - p0),
+ *     t_k = |p_k - o|^2 - |p0 - o|^2,                    (x relative to o)
+ * taken over all edges.  The library evaluates it in float32 on the GPU with
+ * a rigorous per-point error bound, and re-decides the few points inside the
+ * bound exactly, so its answers equal exact closed-polygon membership.
+ *
+ * Conventions shared by every call:
+ *   - Vertices and points are interleaved xy pairs of float32 (PIP_F32) or
+ *     int32 (PIP_I32).  Integer vertices must lie in [-2^24, 2^24].
+ *   - A polygon has 3..64 vertices in either orientation; edge k joins
+ *     vertex k-1 and vertex k (cyclic).
+ *   - The boundary is closed (Eq. 1 uses <=): a point on an edge is inside.
+ *     A point with a NaN or infinite coordinate is outside.
+ *   - Every device pointer is owned by the caller unless stated otherwise;
+ *     the library owns only what pip_prepare allocates inside a pip_tables.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls that do not say "synchronizes" only enqueue work and
+ *     return; they allocate nothing and can be captured in a CUDA graph.
+ *   - Host-detectable argument errors return PIP_E_INVALID_ARG before any
+ *     work is enqueued.  Launch failures return PIP_E_CUDA.  Problems found on
+ *     the device (a bad polygon) are recorded in the tables and reported by
+ *     pip_get_status.
+ */
+#ifndef PIP_H
+#define PIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIP_OK = 0,
+    PIP_E_INVALID_ARG = 1, /* null/misaligned pointer, bad size, n outside 3..64 */
+    PIP_E_DEGENERATE = 2,  /* repeated consecutive vertex, zero area, or a centroid
+                              that is not safely interior (Eq. 4 / Eq. 8 divide by 0) */
+    PIP_E_NONCONVEX = 3,   /* turns both ways, folds back, or winds more than once */
+    PIP_E_NONFINITE = 4,   /* NaN or infinite vertex coordinate */
+    PIP_E_CUDA = 5,        /* a CUDA runtime call failed */
+    PIP_E_TIMEOUT = 6,     /* reserved: a bounded device-side wait ran out */
+    PIP_E_CAPACITY = 7     /* more points than the capacity given to pip_prepare */
+} pip_status;
+
+typedef enum { PIP_F32 = 0, PIP_I32 = 1 } pip_dtype;
+
+/* pip_test output selection (bit flags) */
+enum { PIP_MASK = 1, PIP_FIRST_HIT = 2 };
+
+/* Opaque: device tables built from a batch of polygons (generators,
+ * coefficients, bounds, validation results) plus the refine workspace. */
+typedef struct pip_tables pip_tables;
+
+/*
+ * pip_prepare -- convert polygons into Voronoi generator tables
+ * (Eq. 3-4 / Alg. 3 centroid, Eq. 8 / Alg. 4 generators, and the expanded
+ * Eq. 11 coefficients).  One warp per polygon, in fp64.
+ *
+ *   d_vertices        device, [total_vertices][2] of `vdtype`, 8-byte aligned.
+ *   d_vertex_offsets  device, int32 [num_polygons + 1], non-decreasing,
+ *                     offsets[0] = 0, offsets[num_polygons] = total_vertices.
+ *   num_polygons      >= 1.
+ *   total_vertices    the last offset (the host states it so that nothing
+ *                     has to be read back).
+ *   max_points        the largest num_points any later pip_test call on these
+ *                     tables will pass (sizes the refine queue), >= 0.
+ *   out               receives the new tables; owned by the caller, released
+ *                     with pip_destroy.
+ *
+ * The vertices are copied; the caller's buffers may be freed afterwards.
+ * Allocates device memory (cudaMalloc), so it must not be called while a
+ * stream is being captured.  Per-polygon validation runs on the device; an
+ * invalid polygon contains no point, and pip_get_status reports the worst
+ * problem.  Returns PIP_OK, PIP_E_INVALID_ARG or PIP_E_CUDA.
+ */
+pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype,
+                       const int32_t *d_vertex_offsets, int32_t num_polygons,
+                       int32_t total_vertices, int64_t max_points, void *stream,
+                       pip_tables **out);
+
+/*
+ * pip_test -- Voronoi inclusion (Alg. 5 with the squared-distance form of
+ * Eq. 10-11), bit-exact against exact closed-polygon membership.
+ *
+ *   d_points          device, [num_points][2] of `pdtype`, 8-byte aligned
+ *                     (16-byte alignment takes the vectorised path).
+ *   num_points        0 <= num_points <= max_points of pip_prepare.
+ *   d_point_offsets   NULL: every point meets every polygon.  With one
+ *                     polygon this is the streaming single-polygon test; with
+ *                     several it is the all-pairs test.
+ *                     non-NULL: device int64 [num_polygons + 1]; polygon j
+ *                     owns points [offs[j], offs[j+1]) (own-polygon batch),
+ *                     offs[num_polygons] = num_points.
+ *   mode              PIP_MASK and/or PIP_FIRST_HIT (first hit only when
+ *                     d_point_offsets is NULL).
+ *   d_mask            device uint32 [ceil(num_points / 32)]; bit (i % 32) of
+ *                     word (i / 32) is 1 when point i is inside its polygon
+ *                     (own-polygon batch) or inside at least one polygon
+ *                     (otherwise).  Bits past num_points are written as 0.
+ *   d_first_hit       device int32 [num_points]: the lowest polygon index
+ *                     whose closed polygon holds point i, or -1.  May be NULL
+ *                     when PIP_FIRST_HIT is not requested.
+ *
+ * Points whose float32 result lies within the error bound are queued on the
+ * device and re-decided in fp64 and then exactly (int64 for PIP_I32 inputs,
+ * floating-point expansions for PIP_F32) by a second kernel.  No host
+ * synchronisation; graph-capturable.  Calls on the same tables must not run
+ * concurrently (they share the refine queue).
+ */
+pip_status pip_test(const pip_tables *t, const void *d_points, pip_dtype pdtype,
+                    int64_t num_points, const int64_t *d_point_offsets, int mode,
+                    uint32_t *d_mask, int32_t *d_first_hit, void *stream);
+
+/*
+ * pip_margin -- signed Voronoi margin in length units.  Edge k is the set of
+ * points equidistant from p0 and p_k (Eq. 2); the signed distance of x from
+ * that bisector is (|x - p0|^2 - |x - p_k|^2) / (2 |p_k - p0|), and the margin
+ * is the largest of these over k: > 0 outside, <= 0 inside.  float32, with
+ * error at most a few float32 ulps of the coordinates involved.
+ *
+ *   d_points, num_points, d_point_offsets: as in pip_test.  With
+ *   d_point_offsets NULL and several polygons, the result is the smallest
+ *   margin over all polygons.
+ *   d_margin          device float [num_points].
+ * No host synchronisation; graph-capturable.
+ */
+pip_status pip_margin(const pip_tables *t, const void *d_points, pip_dtype pdtype,
+                      int64_t num_points, const int64_t *d_point_offsets, float *d_margin,
+                      void *stream);
+
+/*
+ * pip_get_status -- synchronizes `stream`, then returns the worst polygon
+ * status found by pip_prepare (PIP_OK if every polygon is valid) and, in
+ * *refine_count (may be NULL), how many points the last pip_test call sent
+ * to the refine step.
+ */
+pip_status pip_get_status(const pip_tables *t, void *stream, int64_t *refine_count);
+
+/* Per-polygon statuses: copies int32 [num_polygons] to host memory (synchronizes). */
+pip_status pip_get_polygon_status(const pip_tables *t, int32_t *h_status, void *stream);
+
+/*
+ * pip_export_tables -- copies the prepared tables to host memory
+ * (synchronizes); any pointer may be NULL to skip that table.
+ *   h_g0     double [num_polygons][2]   centroid p0 (Eq. 4)
+ *   h_gk     double [total_vertices][2] mirrored generators p_k (Eq. 8)
+ *   h_coef   float [total_vertices][4]  (w_x, w_y, t, 0) of edge k, in
+ *                                       coordinates relative to h_origin
+ *   h_origin float [num_polygons][2]    o = float32(p0)
+ *   h_bound  float [num_polygons][2]    (beta0, beta1): |error of s_k| <=
+ *                                       beta0 + beta1 * max(|x|, |y|)
+ */
+pip_status pip_export_tables(const pip_tables *t, double *h_g0, double *h_gk, float *h_coef,
+                             float *h_origin, float *h_bound, void *stream);
+
+/* Releases the tables (synchronizes the device first).  NULL is a no-op. */
+void pip_destroy(pip_tables *t);
+
+/*
+ * Kernel timing, for benchmarks.  pip_timing(t, 1) makes every later pip_test
+ * on `t` record CUDA events on its stream around its bulk kernel and around
+ * its refine kernel (up to 4096 calls are kept); pip_timing(t, 0) stops.
+ * Creating the events synchronizes the device, so call it outside capture.
+ * pip_timing_read synchronizes, returns the number of timed calls and the
+ * summed milliseconds of the bulk and refine kernels, and starts over.
+ */
+pip_status pip_timing(pip_tables *t, int enable);
+pip_status pip_timing_read(pip_tables *t, int32_t *calls, double *bulk_ms, double *refine_ms);
+
+/* Number of polygons / vertices held by the tables. */
+int32_t pip_num_polygons(const pip_tables *t);
+int32_t pip_total_vertices(const pip_tables *t);
+
+const char *pip_status_string(pip_status s);
+
+/* ------------------------------------------------------------------------
+ * Same-chip comparators (the paper's reference tests, Sec. 2.1-2.2, and the
+ * unbatched fp64 form of Alg. 5).  Single polygon or own-polygon batch
+ * (d_point_offsets as in pip_test; NULL needs num_polygons == 1), mask
+ * output as in pip_test.  They are NOT exact: each decides in its own
+ * precision, as the paper's listings do.
+ * ------------------------------------------------------------------------ */
+
+/* Alg. 2 (sign of offset) in float32: inside when every edge's
+ * "LHS < RHS" flag is the same. */
+pip_status pip_test_sign_of_offset(const pip_tables *t, const float *d_points,
+                                   int64_t num_points, const int64_t *d_point_offsets,
+                                   uint32_t *d_mask, void *stream);
+
+/* Alg. 1 (ray crossing, +x ray) in float32; an odd crossing count is inside. */
+pip_status pip_test_ray_crossing(const pip_tables *t, const float *d_points,
+                                 int64_t num_points, const int64_t *d_point_offsets,
+                                 uint32_t *d_mask, void *stream);
+
+/* Alg. 5 literally in fp64: M_0 <= M_k for all k with M the squared distances
+ * to the fp64 generators; no error bound, no refine. */
+pip_status pip_test_voronoi_fp64(const pip_tables *t, const float *d_points,
+                                 int64_t num_points, const int64_t *d_point_offsets,
+                                 uint32_t *d_mask, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIP_H */

@@ -1,0 +1,286 @@
+"""Thin Python binding of libpip (include/pip.h), same names as the C ABI.
+
+Argument marshalling only: every step of the inclusion test runs in the CUDA
+kernels of libpip.so.  PyTorch supplies device memory and the current stream.
+There is no fallback: if libpip.so is missing or a CUDA device is absent the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpip.so")
+
+PIP_OK = 0
+PIP_E_INVALID_ARG = 1
+PIP_E_DEGENERATE = 2
+PIP_E_NONCONVEX = 3
+PIP_E_NONFINITE = 4
+PIP_E_CUDA = 5
+PIP_E_TIMEOUT = 6
+PIP_E_CAPACITY = 7
+PIP_F32 = 0
+PIP_I32 = 1
+PIP_MASK = 1
+PIP_FIRST_HIT = 2
+
+# every symbol include/pip.h declares, with (restype, argtypes)
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_INT = ctypes.c_int
+SIGNATURES = {
+    "pip_prepare": (_INT, [_P, _INT, _P, _I32, _I32, _I64, _P, ctypes.POINTER(_P)]),
+    "pip_test": (_INT, [_P, _P, _INT, _I64, _P, _INT, _P, _P, _P]),
+    "pip_margin": (_INT, [_P, _P, _INT, _I64, _P, _P, _P]),
+    "pip_get_status": (_INT, [_P, _P, ctypes.POINTER(_I64)]),
+    "pip_get_polygon_status": (_INT, [_P, _P, _P]),
+    "pip_export_tables": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
+    "pip_destroy": (None, [_P]),
+    "pip_timing": (_INT, [_P, _INT]),
+    "pip_timing_read": (_INT, [_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)]),
+    "pip_num_polygons": (_I32, [_P]),
+    "pip_total_vertices": (_I32, [_P]),
+    "pip_status_string": (ctypes.c_char_p, [_INT]),
+    "pip_test_sign_of_offset": (_INT, [_P, _P, _I64, _P, _P, _P]),
+    "pip_test_ray_crossing": (_INT, [_P, _P, _I64, _P, _P, _P]),
+    "pip_test_voronoi_fp64": (_INT, [_P, _P, _I64, _P, _P, _P]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class PipError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().pip_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__("%s: %s (status %d)" % (where, msg, status))
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libpip.so (built by paper_2007_15385_gb300.build); raises if it is absent."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise ImportError("libpip.so is not built (%s); run "
+                                      "`python -m paper_2007_15385_gb300.build`" % LIB_PATH)
+                L = ctypes.CDLL(LIB_PATH)
+                for name, (res, args) in SIGNATURES.items():
+                    f = getattr(L, name)
+                    f.restype = res
+                    f.argtypes = args
+                _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != PIP_OK:
+        raise PipError(status, where)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return PIP_F32
+    if t.dtype == torch.int32:
+        return PIP_I32
+    raise TypeError("vertices and points are float32 or int32 xy pairs, got %s" % t.dtype)
+
+
+def _dev(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+class Tables:
+    """Owns one pip_tables handle; released with pip_destroy."""
+
+    def __init__(self, handle: ctypes.c_void_p, num_polygons: int, total_vertices: int,
+                 max_points: int, device: torch.device):
+        self.handle = handle
+        self.num_polygons = num_polygons
+        self.total_vertices = total_vertices
+        self.max_points = max_points
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().pip_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        if not self.handle:
+            raise ValueError("tables already destroyed")
+        return self.handle
+
+
+def pip_prepare(vertices: torch.Tensor, vertex_offsets: torch.Tensor, max_points: int,
+                stream=None) -> Tables:
+    """Polygon -> Voronoi generator tables (Eq. 3-4, Eq. 8)."""
+    _dev(vertices, "vertices")
+    _dev(vertex_offsets, "vertex_offsets")
+    if vertex_offsets.dtype != torch.int32:
+        raise TypeError("vertex_offsets must be int32")
+    P = vertex_offsets.numel() - 1
+    V = vertices.numel() // 2
+    h = ctypes.c_void_p()
+    _check(lib().pip_prepare(vertices.data_ptr(), _dtype_code(vertices), vertex_offsets.data_ptr(),
+                             P, V, int(max_points), _stream(stream), ctypes.byref(h)), "pip_prepare")
+    return Tables(h, P, V, int(max_points), vertices.device)
+
+
+def pip_test(tables: Tables, points: torch.Tensor, point_offsets: torch.Tensor | None = None,
+             mode: int = PIP_MASK, mask: torch.Tensor | None = None,
+             first_hit: torch.Tensor | None = None, stream=None):
+    """Voronoi inclusion (Alg. 5).  Returns (mask uint32 words or None, first_hit or None)."""
+    _dev(points, "points")
+    M = points.numel() // 2
+    if mode & PIP_MASK and mask is None:
+        mask = torch.empty((M + 31) // 32, dtype=torch.int32, device=points.device)
+    if mode & PIP_FIRST_HIT and first_hit is None:
+        first_hit = torch.empty(M, dtype=torch.int32, device=points.device)
+    offs = 0
+    if point_offsets is not None:
+        _dev(point_offsets, "point_offsets")
+        if point_offsets.dtype != torch.int64:
+            raise TypeError("point_offsets must be int64")
+        offs = point_offsets.data_ptr()
+    _check(lib().pip_test(tables, points.data_ptr() if M else None, _dtype_code(points), M,
+                          offs or None, mode, mask.data_ptr() if mask is not None else None,
+                          first_hit.data_ptr() if first_hit is not None else None,
+                          _stream(stream)), "pip_test")
+    return (mask if mode & PIP_MASK else None), (first_hit if mode & PIP_FIRST_HIT else None)
+
+
+def pip_margin(tables: Tables, points: torch.Tensor, point_offsets: torch.Tensor | None = None,
+               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Signed Voronoi margin (Eq. 2 bisector distance), > 0 outside."""
+    _dev(points, "points")
+    M = points.numel() // 2
+    if out is None:
+        out = torch.empty(M, dtype=torch.float32, device=points.device)
+    offs = None
+    if point_offsets is not None:
+        _dev(point_offsets, "point_offsets")
+        offs = point_offsets.data_ptr()
+    _check(lib().pip_margin(tables, points.data_ptr() if M else None, _dtype_code(points), M, offs,
+                            out.data_ptr() if M else None, _stream(stream)), "pip_margin")
+    return out
+
+
+def pip_get_status(tables: Tables, stream=None) -> tuple[int, int]:
+    """(worst polygon status, refine count of the last pip_test); synchronizes."""
+    cnt = ctypes.c_int64(0)
+    st = lib().pip_get_status(tables, _stream(stream), ctypes.byref(cnt))
+    if st == PIP_E_CUDA:
+        raise PipError(st, "pip_get_status")
+    return int(st), int(cnt.value)
+
+
+def pip_get_polygon_status(tables: Tables, stream=None):
+    import numpy as np
+    out = np.zeros(tables.num_polygons, np.int32)
+    _check(lib().pip_get_polygon_status(tables, out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "pip_get_polygon_status")
+    return out
+
+
+def pip_timing(tables: Tables, enable: bool = True):
+    """Turns per-call CUDA-event timing of the bulk and refine kernels on or off."""
+    _check(lib().pip_timing(tables, 1 if enable else 0), "pip_timing")
+
+
+def pip_timing_read(tables: Tables) -> tuple[int, float, float]:
+    """(timed calls, summed bulk-kernel ms, summed refine-kernel ms); synchronizes, resets."""
+    calls = ctypes.c_int32(0)
+    b = ctypes.c_double(0.0)
+    r = ctypes.c_double(0.0)
+    _check(lib().pip_timing_read(tables, ctypes.byref(calls), ctypes.byref(b), ctypes.byref(r)),
+           "pip_timing_read")
+    return int(calls.value), float(b.value), float(r.value)
+
+
+def pip_export_tables(tables: Tables, stream=None) -> dict:
+    import numpy as np
+    P, V = tables.num_polygons, tables.total_vertices
+    g0 = np.zeros((P, 2))
+    gk = np.zeros((V, 2))
+    coef = np.zeros((V, 4), np.float32)
+    origin = np.zeros((P, 2), np.float32)
+    bound = np.zeros((P, 2), np.float32)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().pip_export_tables(tables, ptr(g0), ptr(gk), ptr(coef), ptr(origin), ptr(bound),
+                                   _stream(stream)), "pip_export_tables")
+    return {"g0": g0, "gk": gk, "coef": coef, "origin": origin, "bound": bound}
+
+
+def _cmp(fn: str, tables: Tables, points: torch.Tensor, point_offsets=None, mask=None, stream=None):
+    _dev(points, "points")
+    if points.dtype != torch.float32:
+        raise TypeError("the comparators take float32 points")
+    M = points.numel() // 2
+    if mask is None:
+        mask = torch.empty((M + 31) // 32, dtype=torch.int32, device=points.device)
+    offs = point_offsets.data_ptr() if point_offsets is not None else None
+    _check(getattr(lib(), fn)(tables, points.data_ptr() if M else None, M, offs,
+                              mask.data_ptr() if M else None, _stream(stream)), fn)
+    return mask
+
+
+def pip_test_sign_of_offset(tables, points, point_offsets=None, mask=None, stream=None):
+    """Alg. 2 in float32 on the GPU."""
+    return _cmp("pip_test_sign_of_offset", tables, points, point_offsets, mask, stream)
+
+
+def pip_test_ray_crossing(tables, points, point_offsets=None, mask=None, stream=None):
+    """Alg. 1 in float32 on the GPU."""
+    return _cmp("pip_test_ray_crossing", tables, points, point_offsets, mask, stream)
+
+
+def pip_test_voronoi_fp64(tables, points, point_offsets=None, mask=None, stream=None):
+    """Alg. 5 literally in fp64 on the GPU (unbatched)."""
+    return _cmp("pip_test_voronoi_fp64", tables, points, point_offsets, mask, stream)
+
+
+def unpack_mask(mask: torch.Tensor, num_points: int) -> torch.Tensor:
+    """uint32 words (LSB first) -> uint8 [num_points] on the same device (torch ops: output
+    formatting only, not part of the test)."""
+    w = mask.to(torch.int64) & 0xFFFFFFFF
+    bits = (w.unsqueeze(1) >> torch.arange(32, device=mask.device)) & 1
+    return bits.reshape(-1)[:num_points].to(torch.uint8)
+
+
+def pip_test_host(tables: Tables, points_host: torch.Tensor, device_points: torch.Tensor,
+                  device_mask: torch.Tensor, mask_host: torch.Tensor, stream=None):
+    """End-to-end call on host buffers: pinned host points -> device, pip_test, mask -> pinned
+    host.  The caller provides the device staging buffers, so nothing is allocated per call."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    with torch.cuda.stream(s):
+        device_points.copy_(points_host, non_blocking=True)
+        pip_test(tables, device_points, mask=device_mask, stream=s)
+        mask_host.copy_(device_mask, non_blocking=True)
+    return mask_host

@@ -1,0 +1,68 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU and exports
+every symbol include/pip.h declares; host-side argument checks reject bad
+calls before any device work (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2007_15385_gb300 import binding as B
+from paper_2007_15385_gb300 import build as build_mod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return B.lib()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pip.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pip_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_three_calls():
+    syms = declared_symbols()
+    for s in ("pip_prepare", "pip_test", "pip_margin", "pip_destroy", "pip_get_status"):
+        assert s in syms
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+        assert s in B.SIGNATURES, "binding lacks %s" % s
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert lib.pip_status_string(code)
+    assert b"unknown" in lib.pip_status_string(99)
+
+
+def test_host_argument_checks(lib):
+    out = ctypes.c_void_p()
+    # null pointers / bad sizes are refused before touching the device
+    assert lib.pip_prepare(None, 0, None, 1, 8, 10, None, ctypes.byref(out)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_prepare(8, 0, 8, 0, 8, 10, None, ctypes.byref(out)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_prepare(8, 7, 8, 1, 8, 10, None, ctypes.byref(out)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_prepare(8, 0, 8, 1, 2, 10, None, ctypes.byref(out)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_prepare(8, 0, 8, 1, 65, 10, None, ctypes.byref(out)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_prepare(9, 0, 8, 1, 8, 10, None, ctypes.byref(out)) == B.PIP_E_INVALID_ARG  # misaligned
+    assert lib.pip_prepare(8, 0, 8, 1, 8, -1, None, ctypes.byref(out)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_prepare(8, 0, 8, 1, 8, 1 << 33, None, ctypes.byref(out)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_prepare(8, 0, 8, 1, 8, 10, None, None) == B.PIP_E_INVALID_ARG
+    # calls on a null table handle
+    assert lib.pip_test(None, None, 0, 0, None, 1, None, None, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_margin(None, None, 0, 0, None, None, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_get_status(None, None, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_test_sign_of_offset(None, None, 0, None, None, None) == B.PIP_E_INVALID_ARG
+    lib.pip_destroy(None)  # no-op
+    assert lib.pip_num_polygons(None) == 0
+
+
+def test_build_flags_target_sm103a():
+    assert "arch=compute_103a,code=sm_103a" in build_mod.ARCH

@@ -1,0 +1,487 @@
+"""GPU parity: libpip (through the C ABI) against the CPU oracle.
+
+Masks and first-hit ids must be bit-exact against exact closed-polygon
+membership (oracle.inside_exact / first_hit_exact).  Small cases run the
+oracle on every point; the full-size workloads, in the launch configuration
+the benchmark times, are checked on a random sample of points.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2007_15385_gb300 import binding as B
+from paper_2007_15385_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GUARD = 64
+GUARD_WORD = -0x21524111  # 0xDEADBEEF as int32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.lib()
+    yield
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def guarded(n_words, dtype=torch.int32):
+    buf = torch.full((n_words + 2 * GUARD,), GUARD_WORD, dtype=dtype, device=dev())
+    return buf, buf[GUARD:GUARD + n_words]
+
+
+def check_guards(buf):
+    g = buf.cpu().numpy()
+    assert (g[:GUARD] == GUARD_WORD).all() and (g[-GUARD:] == GUARD_WORD).all(), "guard zone written"
+
+
+def run_test(w, mode=B.PIP_MASK, points_offset=0):
+    """Runs pip_test on workload w; returns (inside uint8[M] or None, first_hit or None, refine)."""
+    v = torch.from_numpy(np.ascontiguousarray(w.vertices)).to(dev())
+    vo = torch.from_numpy(np.ascontiguousarray(w.vertex_offsets)).to(dev())
+    M = w.num_points
+    flat = np.zeros(2 * (M + points_offset), w.points.dtype)
+    flat[2 * points_offset:] = w.points.reshape(-1)
+    pbuf = torch.from_numpy(flat).to(dev())
+    p = pbuf[2 * points_offset:]
+    po = None
+    if w.point_offsets is not None:
+        po = torch.from_numpy(np.ascontiguousarray(w.point_offsets)).to(dev())
+    t = B.pip_prepare(v, vo, max_points=M)
+    nwords = (M + 31) // 32
+    mbuf, mask = guarded(nwords)
+    hbuf = hit = None
+    if mode & B.PIP_FIRST_HIT:
+        hbuf, hit = guarded(M)
+    B.pip_test(t, p, po, mode=mode, mask=mask if mode & B.PIP_MASK else None, first_hit=hit)
+    st, refine = B.pip_get_status(t)
+    inside = None
+    if mode & B.PIP_MASK:
+        check_guards(mbuf)
+        words = mask.cpu().numpy().view(np.uint32)
+        if M % 32:
+            assert words[-1] >> (M % 32) == 0, "bits past num_points must be 0"
+        inside = np.unpackbits(words.view(np.uint8), bitorder="little")[:M]
+    fh = None
+    if hit is not None:
+        check_guards(hbuf)
+        fh = hit.cpu().numpy()
+    t.close()
+    return inside, fh, refine, st
+
+
+def oracle_own(w):
+    if w.point_offsets is None:
+        out, st = oracle.inside_exact(w.vertices, w.points)
+        return out
+    out, st = oracle.inside_exact_ragged(w.vertices, w.vertex_offsets, w.points, w.point_offsets)
+    return out
+
+
+def assert_same(got, want, what):
+    bad = np.nonzero(got != want)[0]
+    assert len(bad) == 0, "%s: %d mismatches, first at %s" % (what, len(bad), bad[:10].tolist())
+
+
+# ----------------------------------------------------------------- small, every point
+
+def test_octagon_full_size():
+    w = wl.unit_circle_octagon()
+    got, _, refine, st = run_test(w)
+    assert st == B.PIP_OK
+    assert_same(got, oracle_own(w), "octagon")
+
+
+@pytest.mark.parametrize("m", [1, 31, 33, 63, 64, 65, 257, 100_003])
+def test_vehicle_footprint_ragged_tails(m):
+    w = wl.vehicle_footprint(m=m)
+    got, _, _, _ = run_test(w)
+    assert_same(got, oracle_own(w), "footprint m=%d" % m)
+
+
+def test_vehicle_footprint_million_unaligned_points():
+    # points start 8 bytes past a 16-byte boundary: the non-vector load path
+    w = wl.vehicle_footprint(m=1_000_003)
+    got, _, _, _ = run_test(w, points_offset=1)
+    assert_same(got, oracle_own(w), "footprint unaligned")
+
+
+def test_empty_point_set():
+    w = wl.vehicle_footprint(m=0)
+    got, _, refine, st = run_test(w)
+    assert got.size == 0 and refine == 0
+
+
+def test_gis_batch_small():
+    w = wl.gis_batch(seed=12, num_polygons=64, m_range=(100, 5000))
+    got, _, refine, st = run_test(w)
+    assert st == B.PIP_OK
+    assert_same(got, oracle_own(w), "gis small")
+
+
+def test_gis_batch_with_empty_and_tiny_polygons():
+    w = wl.gis_batch(seed=13, num_polygons=40, m_range=(0, 70))
+    got, _, _, _ = run_test(w)
+    assert_same(got, oracle_own(w), "gis tiny")
+
+
+def test_all_pairs_first_hit_small():
+    w = wl.gis_all_pairs(seed=14, num_polygons=96, m=30_011, total_polygons=96)
+    got, fh, refine, st = run_test(w, mode=B.PIP_MASK | B.PIP_FIRST_HIT)
+    want = oracle.first_hit_exact(w.vertices, w.vertex_offsets, w.points)
+    assert_same(fh, want, "first hit")
+    assert_same(got, (want >= 0).astype(np.uint8), "all-pairs mask")
+
+
+def test_all_pairs_mask_only():
+    w = wl.gis_all_pairs(seed=15, num_polygons=40, m=5_000, total_polygons=40)
+    got, _, _, _ = run_test(w, mode=B.PIP_MASK)
+    want = oracle.first_hit_exact(w.vertices, w.vertex_offsets, w.points)
+    assert_same(got, (want >= 0).astype(np.uint8), "all-pairs mask only")
+
+
+def test_integer_hulls_small():
+    w = wl.integer_hulls(seed=16, num_polygons=48, points_per_polygon=3000)
+    got, _, refine, st = run_test(w)
+    assert st == B.PIP_OK
+    assert_same(got, oracle_own(w), "integer hulls")
+    # on-edge and one-off points dominate the refine queue
+    assert refine > 0.2 * w.num_points
+
+
+def test_integer_points_beyond_float_range():
+    v = np.array([[-1000, -1000], [1000, -1000], [1000, 1000], [-1000, 1000]], np.int32)
+    pts = np.array([[0, 0], [1000, 0], [1001, 0], [2 ** 30, 5], [-2 ** 31, 0], [2 ** 31 - 1, 2 ** 31 - 1],
+                    [1000, 1000], [-1000, -1001]], np.int32)
+    w = wl.Workload("big", v, np.array([0, 4], np.int32), pts)
+    got, _, _, _ = run_test(w)
+    assert_same(got, oracle_own(w), "big ints")
+
+
+def test_nonfinite_points_are_outside():
+    v = wl.regular_polygon(6, 1.0).astype(np.float32)
+    pts = np.array([[0, 0], [np.nan, 0], [0, np.inf], [-np.inf, np.inf], [np.inf, np.inf],
+                    [np.nan, np.nan], [0.5, 0.1]], np.float32)
+    w = wl.Workload("nan", v, np.array([0, 6], np.int32), pts)
+    got, _, _, _ = run_test(w)
+    assert got.tolist() == [1, 0, 0, 0, 0, 0, 1]
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 17, 33, 63, 64])
+@pytest.mark.parametrize("cw", [False, True])
+def test_vertex_counts_and_orientation(n, cw):
+    rng = np.random.default_rng(n)
+    v = wl._circle_polygon(rng, n, 3.0, -2.0, 1.7, 0.9)
+    if cw:
+        v = v[::-1].copy()
+    pts = rng.uniform(-1, 6, size=(20_000, 2)).astype(np.float32) + np.array([0, -5], np.float32)
+    w = wl.Workload("n", v, np.array([0, n], np.int32), pts)
+    got, _, _, st = run_test(w)
+    assert st == B.PIP_OK
+    assert_same(got, oracle_own(w), "n=%d cw=%s" % (n, cw))
+
+
+def _edge_sweep(v, rng, per_edge=200, ulps=3):
+    out = [v]
+    n = len(v)
+    for k in range(n):
+        a, b = v[k - 1].astype(np.float64), v[k].astype(np.float64)
+        t = rng.random(per_edge)
+        q = (a + t[:, None] * (b - a)).astype(np.float32)
+        out.append(q)
+        for dx in range(-ulps, ulps + 1):
+            for dy in range(-ulps, ulps + 1):
+                if dx == 0 and dy == 0:
+                    continue
+                qq = q.copy()
+                for _ in range(abs(dx)):
+                    qq[:, 0] = np.nextafter(qq[:, 0], np.float32(np.sign(dx) * np.inf))
+                for _ in range(abs(dy)):
+                    qq[:, 1] = np.nextafter(qq[:, 1], np.float32(np.sign(dy) * np.inf))
+                out.append(qq)
+    return np.concatenate(out).astype(np.float32)
+
+
+@pytest.mark.parametrize("centre", [(0.0, 0.0), (1e4, -3e3), (1e6, 1e6)])
+def test_ulp_sweep_around_edges(centre):
+    rng = np.random.default_rng(17)
+    v = wl._circle_polygon(rng, 9, centre[0], centre[1], 2.5, 1.0)
+    pts = _edge_sweep(v, rng)
+    w = wl.Workload("ulp", v, np.array([0, len(v)], np.int32), pts)
+    got, _, refine, st = run_test(w)
+    assert st == B.PIP_OK
+    assert_same(got, oracle_own(w), "ulp sweep at %s" % (centre,))
+    assert refine > 0
+
+
+def test_sliver_polygons_exact_or_rejected():
+    rng = np.random.default_rng(18)
+    for s in (1e-2, 1e-4, 1e-6):
+        v = np.array([[0, 0], [1000, 0], [2000, s * 1000], [1000, s * 2000]], np.float32)
+        if oracle.polygon_status(v) != oracle.OK:
+            continue
+        pts = np.concatenate([_edge_sweep(v, rng, 50, 2),
+                              rng.uniform([-10, -1], [2010, 25], size=(5000, 2)).astype(np.float32)])
+        w = wl.Workload("sliver", v, np.array([0, 4], np.int32), pts)
+        got, _, _, st = run_test(w)
+        if st == B.PIP_OK:
+            assert_same(got, oracle_own(w), "sliver %g" % s)
+        else:
+            assert st == B.PIP_E_DEGENERATE and not got.any()
+
+
+def test_invalid_polygons_report_status_and_hold_nothing():
+    sq = [[0, 0], [4, 0], [4, 4], [0, 4]]
+    polys = [
+        sq,                                           # ok
+        [[0, 0], [2, 0], [1, 0.2], [2, 2], [0, 2]],   # non-convex
+        [[0, 0], [1, 0], [1, 0], [0, 1]],             # repeated vertex
+        [[0, 0], [1, 0], [2, 0]],                     # zero area
+        [[0, 0], [1, np.nan], [1, 1]],                # NaN vertex
+        list(wl.regular_polygon(5, 1.0)[[0, 2, 4, 1, 3]]),  # winds twice
+        sq,
+    ]
+    verts = np.concatenate([np.array(p, np.float32) for p in polys])
+    voffs = np.zeros(len(polys) + 1, np.int32)
+    voffs[1:] = np.cumsum([len(p) for p in polys])
+    v = torch.from_numpy(verts).to(dev())
+    vo = torch.from_numpy(voffs).to(dev())
+    t = B.pip_prepare(v, vo, max_points=1000)
+    st = B.pip_get_polygon_status(t)
+    want = [oracle.polygon_status(np.array(p, np.float64)) for p in polys]
+    assert st.tolist() == want
+    worst, _ = B.pip_get_status(t)
+    assert worst == max(want)
+    # every point is offered to every polygon: only the two squares hold any
+    pts = np.array([[1, 1], [0.5, 0.5], [3, 3], [0, 0]], np.float32)
+    _, fh = B.pip_test(t, torch.from_numpy(pts).to(dev()), mode=B.PIP_FIRST_HIT | B.PIP_MASK)
+    assert fh.cpu().numpy().tolist() == [0, 0, 0, 0]
+    t.close()
+
+
+def test_polygon_vertex_count_limits():
+    v = torch.from_numpy(wl.regular_polygon(70, 1.0).astype(np.float32)).to(dev())
+    vo = torch.tensor([0, 2, 70], dtype=torch.int32, device=dev())
+    t = B.pip_prepare(v, vo, max_points=10)
+    st = B.pip_get_polygon_status(t)
+    assert st.tolist() == [B.PIP_E_INVALID_ARG, B.PIP_E_INVALID_ARG]
+    t.close()
+
+
+def test_capacity_is_enforced():
+    w = wl.vehicle_footprint(m=100)
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    t = B.pip_prepare(v, vo, max_points=50)
+    p = torch.from_numpy(w.points).to(dev())
+    with pytest.raises(B.PipError) as e:
+        B.pip_test(t, p)
+    assert e.value.status == B.PIP_E_CAPACITY
+    t.close()
+
+
+def test_prepare_tables_match_oracle():
+    w = wl.gis_batch(seed=19, num_polygons=50, m_range=(1, 2))
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    t = B.pip_prepare(v, vo, max_points=1)
+    tab = B.pip_export_tables(t)
+    for j in range(w.num_polygons):
+        vv = w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]]
+        area, c = oracle.centroid(vv)
+        g = oracle.generators(vv, c)
+        scale = np.abs(vv).max() + 1.0
+        np.testing.assert_allclose(tab["g0"][j], c, atol=1e-12 * scale, rtol=0)
+        gk = tab["gk"][w.vertex_offsets[j]:w.vertex_offsets[j + 1]]
+        np.testing.assert_allclose(gk, g, atol=1e-10 * scale, rtol=0)
+        o = tab["origin"][j].astype(np.float64)
+        np.testing.assert_allclose(o, c, rtol=2 ** -23)
+        cf = tab["coef"][w.vertex_offsets[j]:w.vertex_offsets[j + 1]].astype(np.float64)
+        wk = 2 * (g - c)
+        tk = ((g - o) ** 2).sum(1) - ((c - o) ** 2).sum(1)
+        tol_w = 2 ** -22 * np.abs(wk).max() + 1e-9 * scale
+        np.testing.assert_allclose(cf[:, :2], wk, atol=tol_w, rtol=0)
+        np.testing.assert_allclose(cf[:, 2], tk, atol=2 ** -22 * np.abs(tk).max() + 1e-9 * scale ** 2, rtol=0)
+    t.close()
+
+
+def test_margin_matches_oracle():
+    w = wl.vehicle_footprint(m=50_001)
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    p = torch.from_numpy(w.points).to(dev())
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    got = B.pip_margin(t, p).cpu().numpy().astype(np.float64)
+    want = oracle.margin(w.vertices, w.points)
+    # float32 evaluation relative to o: a few ulps of |x| and |t|
+    tol = 8 * 2 ** -24 * (np.abs(w.points).max(axis=1) + 4.0)
+    assert np.all(np.abs(got - want) <= tol)
+    # sign agrees with the exact mask wherever the margin is clearly away from 0
+    inside = oracle_own(w)
+    far = np.abs(want) > 1e-5
+    assert ((want[far] <= 0) == inside[far].astype(bool)).all()
+    t.close()
+
+
+def test_margin_ragged_and_all_pairs():
+    w = wl.gis_batch(seed=20, num_polygons=30, m_range=(10, 3000))
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    p = torch.from_numpy(w.points).to(dev())
+    po = torch.from_numpy(w.point_offsets).to(dev())
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    got = B.pip_margin(t, p, po).cpu().numpy().astype(np.float64)
+    for j in range(w.num_polygons):
+        sl = slice(w.point_offsets[j], w.point_offsets[j + 1])
+        vv = w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]]
+        want = oracle.margin(vv, w.points[sl])
+        tol = 16 * 2 ** -24 * (np.abs(w.points[sl] - vv.mean(0)).max(axis=1) + np.abs(vv).max() * 1e-3 + 1.0) * 64
+        assert np.all(np.abs(got[sl] - want) <= tol), j
+    # all pairs: the smallest margin over the polygons
+    sub = w.points[:2000]
+    allm = B.pip_margin(t, torch.from_numpy(sub).to(dev())).cpu().numpy()
+    want = np.min([oracle.margin(w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]], sub)
+                   for j in range(w.num_polygons)], axis=0)
+    np.testing.assert_allclose(allm, want, atol=0.05, rtol=1e-4)
+    t.close()
+
+
+def _distance_to_edges(v, q):
+    d = np.full(len(q), np.inf)
+    for k in range(len(v)):
+        a, b = v[k - 1].astype(float), v[k].astype(float)
+        e = b - a
+        cr = e[0] * (q[:, 1] - a[1]) - e[1] * (q[:, 0] - a[0])
+        d = np.minimum(d, np.abs(cr) / np.linalg.norm(e))
+    return d
+
+
+def test_comparators_agree_off_boundary():
+    w = wl.vehicle_footprint(m=300_001)
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    p = torch.from_numpy(w.points).to(dev())
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    want = oracle_own(w)
+    far = _distance_to_edges(w.vertices, w.points) > 1e-4
+    for fn in (B.pip_test_sign_of_offset, B.pip_test_ray_crossing, B.pip_test_voronoi_fp64):
+        m = fn(t, p)
+        got = B.unpack_mask(m, w.num_points).cpu().numpy()
+        assert_same(got[far], want[far], fn.__name__)
+    t.close()
+
+
+def test_comparators_ragged():
+    w = wl.gis_batch(seed=21, num_polygons=20, m_range=(50, 2000))
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    p = torch.from_numpy(w.points).to(dev())
+    po = torch.from_numpy(w.point_offsets).to(dev())
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    want = oracle_own(w)
+    for fn in (B.pip_test_sign_of_offset, B.pip_test_ray_crossing, B.pip_test_voronoi_fp64):
+        got = B.unpack_mask(fn(t, p, po), w.num_points).cpu().numpy()
+        agree = (got == want).mean()
+        assert agree > 0.9999, (fn.__name__, agree)
+    t.close()
+
+
+def test_repeated_calls_reset_the_refine_queue():
+    w = wl.integer_hulls(seed=22, num_polygons=8, points_per_polygon=1000)
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    p = torch.from_numpy(w.points).to(dev())
+    po = torch.from_numpy(w.point_offsets).to(dev())
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    want = oracle_own(w)
+    counts = []
+    for _ in range(3):
+        mask, _ = B.pip_test(t, p, po)
+        counts.append(B.pip_get_status(t)[1])
+        assert_same(B.unpack_mask(mask, w.num_points).cpu().numpy(), want, "repeat")
+    assert counts[0] == counts[1] == counts[2]
+    t.close()
+
+
+def test_cuda_graph_capture_of_pip_test():
+    w = wl.gis_batch(seed=23, num_polygons=16, m_range=(100, 4000))
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    p = torch.from_numpy(w.points).to(dev())
+    po = torch.from_numpy(w.point_offsets).to(dev())
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    mask = torch.zeros((w.num_points + 31) // 32, dtype=torch.int32, device=dev())
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        B.pip_test(t, p, po, mask=mask, stream=s)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    mask.zero_()
+    with torch.cuda.graph(g):
+        B.pip_test(t, p, po, mask=mask)
+    g.replay()
+    torch.cuda.synchronize()
+    got = B.unpack_mask(mask, w.num_points).cpu().numpy()
+    assert_same(got, oracle_own(w), "graph replay")
+    t.close()
+
+
+# ----------------------------------------------------------------- full size, sampled
+
+def _sample(rng, M, k):
+    return np.unique(np.concatenate([rng.integers(0, M, size=k), np.arange(min(M, 64)),
+                                     np.arange(max(0, M - 64), M)]))
+
+
+def test_vehicle_footprint_full_size_sampled():
+    w = wl.vehicle_footprint()
+    got, _, refine, st = run_test(w)
+    rng = np.random.default_rng(0)
+    idx = _sample(rng, w.num_points, 300_000)
+    want, _ = oracle.inside_exact(w.vertices, w.points[idx])
+    assert_same(got[idx], want, "footprint 2^26 sample")
+
+
+def test_gis_batch_full_size_sampled():
+    w = wl.gis_batch()
+    got, _, refine, st = run_test(w)
+    assert st == B.PIP_OK
+    rng = np.random.default_rng(1)
+    for j in rng.choice(w.num_polygons, size=256, replace=False):
+        a, b = w.point_offsets[j], w.point_offsets[j + 1]
+        idx = np.unique(np.concatenate([rng.integers(a, b, size=200), [a, b - 1]]))
+        vv = w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]]
+        want, _ = oracle.inside_exact(vv, w.points[idx])
+        assert_same(got[idx], want, "gis polygon %d" % j)
+
+
+def test_all_pairs_full_size_sampled():
+    w = wl.gis_all_pairs()
+    _, fh, _, _ = run_test(w, mode=B.PIP_FIRST_HIT | B.PIP_MASK)
+    rng = np.random.default_rng(2)
+    idx = rng.choice(w.num_points, size=4000, replace=False)
+    want = oracle.first_hit_exact(w.vertices, w.vertex_offsets, w.points[idx])
+    assert_same(fh[idx], want, "all pairs sample")
+
+
+def test_integer_hulls_full_size_sampled():
+    w = wl.integer_hulls()
+    got, _, refine, st = run_test(w)
+    assert st == B.PIP_OK
+    rng = np.random.default_rng(3)
+    for j in rng.choice(w.num_polygons, size=128, replace=False):
+        a, b = w.point_offsets[j], w.point_offsets[j + 1]
+        idx = np.arange(a, b)[::16]
+        vv = w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]]
+        want, _ = oracle.inside_exact(vv, w.points[idx])
+        assert_same(got[idx], want, "hull %d" % j)
