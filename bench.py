@@ -182,6 +182,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--points", type=int, default=NUM_POINTS,
+                    help="points of the workload (default the full 2^26; smaller only for profiling)")
+    ap.add_argument("--min-warmup-s", type=float, default=1.0,
+                    help="warm up for at least this long so that clocks settle")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -202,7 +206,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = wl.vehicle_footprint(m=NUM_POINTS)
+    w = wl.vehicle_footprint(m=args.points)
     M = w.num_points
     n = int(w.edges()[0])
     v = torch.from_numpy(w.vertices).to(dev)
@@ -230,7 +234,7 @@ def main():
     # warm-up: W steps, and at least 1 s of them so that clocks settle
     t_w = time.perf_counter()
     i = 0
-    while i < args.warmup or time.perf_counter() - t_w < 1.0:
+    while i < args.warmup or time.perf_counter() - t_w < args.min_warmup_s:
         B.pip_test(t, p, mask=mask)
         i += 1
         if i % 100 == 0:

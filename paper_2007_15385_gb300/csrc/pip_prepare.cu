@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(
         if (nonfinite) status = PIP_E_NONFINITE;
         else if (int_bad) status = PIP_E_INVALID_ARG;
         else if (zero_edge) status = PIP_E_DEGENERATE;
+        else if (!pos && !neg) status = PIP_E_DEGENERATE;           // all collinear: zero area
         else if ((pos && neg) || fold) status = PIP_E_NONCONVEX;
-        else if (!pos && !neg) status = PIP_E_DEGENERATE;           // all collinear
         else if (fabs(turn) > 3.0 * M_PI) status = PIP_E_NONCONVEX;  // winds twice or more
         else if (!(S * (pos ? 1.0 : -1.0) > 0.0)) status = PIP_E_DEGENERATE;
     }

@@ -473,6 +473,11 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     if (num_points > t->capacity) return PIP_E_CAPACITY;
     if ((mode & ~(PIP_MASK | PIP_FIRST_HIT)) || mode == 0) return PIP_E_INVALID_ARG;
     const bool want_mask = mode & PIP_MASK, want_hit = mode & PIP_FIRST_HIT;
+    if (want_hit && d_point_offsets != nullptr) return PIP_E_INVALID_ARG;
+    if (num_points == 0) {  // nothing to decide; the refine count of this call is 0
+        PIP_CUDA_TRY(cudaMemsetAsync(t->d_qcount, 0, sizeof(unsigned int), (cudaStream_t)stream));
+        return PIP_OK;
+    }
     if (want_mask && d_mask == nullptr) return PIP_E_INVALID_ARG;
     if (want_hit && (d_first_hit == nullptr || d_point_offsets != nullptr)) return PIP_E_INVALID_ARG;
     if (num_points > 0 && (d_points == nullptr || !aligned(d_points, 8))) return PIP_E_INVALID_ARG;

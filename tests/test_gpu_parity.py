@@ -306,7 +306,7 @@ def test_prepare_tables_match_oracle():
         np.testing.assert_allclose(o, c, rtol=2 ** -23)
         cf = tab["coef"][w.vertex_offsets[j]:w.vertex_offsets[j + 1]].astype(np.float64)
         wk = 2 * (g - c)
-        tk = ((g - o) ** 2).sum(1) - ((c - o) ** 2).sum(1)
+        tk = ((g - o) ** 2).sum(1) - ((c - o) ** 2).sum()
         tol_w = 2 ** -22 * np.abs(wk).max() + 1e-9 * scale
         np.testing.assert_allclose(cf[:, :2], wk, atol=tol_w, rtol=0)
         np.testing.assert_allclose(cf[:, 2], tk, atol=2 ** -22 * np.abs(tk).max() + 1e-9 * scale ** 2, rtol=0)
