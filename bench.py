@@ -40,8 +40,8 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per launch of the streaming kernel on this
 # workload, from one ncu capture (profiles/stream_kernel_vehicle_footprint.md),
 # valid only while the kernel sources hash to the value recorded with it.
-NCU_TRAFFIC = {"bytes": 549259264, "sources_sha": "c99d5fee689be663"}
-KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_test.cu",
+NCU_TRAFFIC = {"bytes": 549259264, "sources_sha": "a0aef079207fae9c"}
+KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_test_kernels.cuh",
                   "paper_2007_15385_gb300/csrc/pip_kernels.cuh",
                   "paper_2007_15385_gb300/csrc/pip_internal.cuh"]
 

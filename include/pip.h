@@ -210,6 +210,39 @@ pip_status pip_test_voronoi_fp64(const pip_tables *t, const float *d_points,
                                  int64_t num_points, const int64_t *d_point_offsets,
                                  uint32_t *d_mask, void *stream);
 
+/* ------------------------------------------------------------------------
+ * pip_test_single_noalloc -- the paper has no counterpart to this call; it
+ * exists for callers that cannot allocate device memory when they test
+ * points: a fixed-rate control loop (a vehicle's collision check) that cannot
+ * absorb cudaMalloc's latency and implicit synchronisation, or a plug-in
+ * whose host application owns the device memory pool or a fixed memory
+ * budget.  It does what pip_prepare + pip_test + pip_destroy do for ONE
+ * polygon and a mask, with the same exact result, but allocates nothing: its
+ * scratch (the polygon's tables and the refine queue, about 4 MiB) is one
+ * static device array that every GPU loading this library holds until the
+ * process exits.
+ *
+ *   d_vertices    device, [num_vertices][2] of `vdtype`, 8-byte aligned.
+ *   num_vertices  3..64.
+ *   d_points      device, [num_points][2] of `pdtype`, 8-byte aligned.
+ *   num_points    0 .. 1048576 (2^20); more returns PIP_E_CAPACITY and
+ *                 enqueues nothing.
+ *   d_mask        device uint32 [ceil(num_points / 32)], as in pip_test.
+ *   d_status      device int32 [1] or NULL: receives the polygon's status
+ *                 (PIP_OK or the pip_prepare code; an invalid polygon
+ *                 contains no point).
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one scratch array and it
+ * keeps the last call's contents (each call clears its own counters first):
+ * calls that overlap on the GPU -- on different streams, or from host threads
+ * without ordering -- race on it and must not be issued.
+ * ------------------------------------------------------------------------ */
+pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype vdtype, int32_t num_vertices,
+                                   const void *d_points, pip_dtype pdtype, int64_t num_points,
+                                   uint32_t *d_mask, int32_t *d_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,7 @@ SIGNATURES = {
     "pip_test_sign_of_offset": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "pip_test_ray_crossing": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "pip_test_voronoi_fp64": (_INT, [_P, _P, _I64, _P, _P, _P]),
+    "pip_test_single_noalloc": (_INT, [_P, _INT, _I32, _P, _INT, _I64, _P, _P, _P]),
 }
 
 _lib = None
@@ -284,3 +285,23 @@ def pip_test_host(tables: Tables, points_host: torch.Tensor, device_points: torc
         pip_test(tables, device_points, mask=device_mask, stream=s)
         mask_host.copy_(device_mask, non_blocking=True)
     return mask_host
+
+
+NOALLOC_MAX_POINTS = 1 << 20
+
+
+def pip_test_single_noalloc(vertices: torch.Tensor, points: torch.Tensor, mask: torch.Tensor,
+                            status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One polygon against points with no device allocation inside the call (for callers that
+    cannot allocate: fixed-rate control loops, hosts that own the memory pool).  The caller
+    passes every buffer; scratch is a static array inside libpip shared by all calls."""
+    _dev(vertices, "vertices")
+    _dev(points, "points")
+    _dev(mask, "mask")
+    M = points.numel() // 2
+    _check(lib().pip_test_single_noalloc(vertices.data_ptr(), _dtype_code(vertices),
+                                         vertices.numel() // 2, points.data_ptr() if M else None,
+                                         _dtype_code(points), M, mask.data_ptr() if M else None,
+                                         status.data_ptr() if status is not None else None,
+                                         _stream(stream)), "pip_test_single_noalloc")
+    return mask
