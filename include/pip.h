@@ -179,6 +179,21 @@ void pip_destroy(pip_tables *t);
 pip_status pip_timing(pip_tables *t, int enable);
 pip_status pip_timing_read(pip_tables *t, int32_t *calls, double *bulk_ms, double *refine_ms);
 
+/*
+ * Tile shapes of the pipelined single-polygon kernel (the path pip_test takes
+ * for one polygon, no point offsets and 16-byte aligned points): each variant
+ * is (points per lane per stage, ring stages).  pip_autotune_stream times
+ * every variant `reps` times with CUDA events on the caller's own inputs
+ * (synchronizes; not during capture), keeps the fastest in the tables and
+ * returns it with its mean milliseconds.  pip_set_stream_variant picks one
+ * directly (for a cached tuning result).
+ */
+int32_t pip_stream_variant_count(void);
+pip_status pip_set_stream_variant(pip_tables *t, int32_t variant);
+pip_status pip_autotune_stream(pip_tables *t, const void *d_points, pip_dtype pdtype,
+                               int64_t num_points, uint32_t *d_mask, int32_t reps, void *stream,
+                               int32_t *best_variant, float *best_ms);
+
 /* Number of polygons / vertices held by the tables. */
 int32_t pip_num_polygons(const pip_tables *t);
 int32_t pip_total_vertices(const pip_tables *t);

@@ -52,6 +52,10 @@ SIGNATURES = {
     "pip_test_ray_crossing": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "pip_test_voronoi_fp64": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "pip_test_single_noalloc": (_INT, [_P, _INT, _I32, _P, _INT, _I64, _P, _P, _P]),
+    "pip_stream_variant_count": (_I32, []),
+    "pip_set_stream_variant": (_INT, [_P, _I32]),
+    "pip_autotune_stream": (_INT, [_P, _P, _INT, _I64, _P, _I32, _P, ctypes.POINTER(_I32),
+                                    ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lib = None
@@ -223,6 +227,27 @@ def pip_timing_read(tables: Tables) -> tuple[int, float, float]:
     _check(lib().pip_timing_read(tables, ctypes.byref(calls), ctypes.byref(b), ctypes.byref(r)),
            "pip_timing_read")
     return int(calls.value), float(b.value), float(r.value)
+
+
+def pip_stream_variant_count() -> int:
+    return int(lib().pip_stream_variant_count())
+
+
+def pip_set_stream_variant(tables: Tables, variant: int):
+    _check(lib().pip_set_stream_variant(tables, int(variant)), "pip_set_stream_variant")
+
+
+def pip_autotune_stream(tables: Tables, points: torch.Tensor, mask: torch.Tensor, reps: int = 5,
+                        stream=None) -> tuple[int, float]:
+    """Times every tile shape of the pipelined kernel on these inputs; keeps the fastest."""
+    _dev(points, "points")
+    best = ctypes.c_int32(-1)
+    ms = ctypes.c_float(0.0)
+    _check(lib().pip_autotune_stream(tables, points.data_ptr(), _dtype_code(points),
+                                     points.numel() // 2, mask.data_ptr(), int(reps),
+                                     _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
+           "pip_autotune_stream")
+    return int(best.value), float(ms.value)
 
 
 def pip_export_tables(tables: Tables, stream=None) -> dict:

@@ -93,6 +93,9 @@ struct pip_tables {
     unsigned int *d_qcount;      // refine queue length of the last pip_test
     unsigned int *d_work;        // next work item of the persistent kernel
     int32_t *d_worst;            // worst polygon status
+    int32_t *d_error;            // runtime error of a kernel (PIP_E_TIMEOUT), sticky until read
+    void *d_stream_ctr;          // counters of the pipelined kernel (zero between launches)
+    int stream_variant;          // tile shape of the pipelined single-polygon kernel
     // pip_timing: event triples (before bulk, after bulk, after refine)
     int timing;
     int timed_calls;
@@ -122,6 +125,10 @@ namespace pip {
 // Host helpers implemented in pip_prepare.cu.
 pip_status check_tables(const pip_tables *t);
 bool aligned(const void *p, size_t a);
+// Implemented in pip_test.cu: raises the dynamic shared-memory limit of the
+// pipelined kernels on the current device (outside any stream capture).
+cudaError_t stream_kernels_setup();
+int stream_variant_count();
 }  // namespace pip
 
 namespace pip {

@@ -81,7 +81,7 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     const size_t o_coefn = take(V * sizeof(float4));
     const size_t o_poly = take(P * sizeof(PolyInfo));
     const size_t o_items = take((P + 1) * sizeof(int64_t));
-    const size_t o_cnt = take(64);
+    const size_t o_cnt = take(128);
     const size_t o_queue = take((size_t)(max_points > 0 ? max_points : 1) * sizeof(uint32_t));
     t->bytes = off;
     if (cudaMalloc(&t->base, t->bytes) != cudaSuccess) {
@@ -100,6 +100,8 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     t->d_qcount = (unsigned int *)(b + o_cnt);
     t->d_work = (unsigned int *)(b + o_cnt + 16);
     t->d_worst = (int32_t *)(b + o_cnt + 32);
+    t->d_error = (int32_t *)(b + o_cnt + 48);
+    t->d_stream_ctr = (void *)(b + o_cnt + 64);
     t->d_queue = (uint32_t *)(b + o_queue);
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -107,7 +109,8 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_verts, d_vertices, V * 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(t->d_voffs, d_vertex_offsets, (P + 1) * 4, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt, 0, 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt, 0, 128, s);
+    if (e == cudaSuccess) e = stream_kernels_setup();
     if (e == cudaSuccess) {
         const int threads = 256;
         const int blocks = (int)((P * 32 + threads - 1) / threads);
@@ -189,8 +192,14 @@ pip_status pip_get_status(const pip_tables *t, void *stream, int64_t *refine_cou
     pip_status st = check_tables(t);
     if (st != PIP_OK) return st;
     PIP_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    int32_t worst = 0;
+    int32_t worst = 0, error = 0;
     unsigned int cnt = 0;
+    PIP_CUDA_TRY(cudaMemcpy(&error, t->d_error, sizeof(error), cudaMemcpyDeviceToHost));
+    if (error != 0) {
+        PIP_CUDA_TRY(cudaMemset(t->d_error, 0, sizeof(int32_t)));
+        if (refine_count) *refine_count = 0;
+        return (pip_status)error;
+    }
     PIP_CUDA_TRY(cudaMemcpy(&worst, t->d_worst, sizeof(worst), cudaMemcpyDeviceToHost));
     PIP_CUDA_TRY(cudaMemcpy(&cnt, t->d_qcount, sizeof(cnt), cudaMemcpyDeviceToHost));
     if (refine_count) *refine_count = (int64_t)cnt;

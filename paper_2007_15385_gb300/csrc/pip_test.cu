@@ -23,6 +23,7 @@
 using namespace pip;
 
 #include "pip_test_kernels.cuh"
+#include "pip_stream_tma.cuh"
 
 namespace {
 
@@ -63,7 +64,72 @@ cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int
     return cudaGetLastError();
 }
 
+// Tile shapes of the pipelined kernel: (points per lane per stage, stages).
+struct StreamVariant {
+    int ppl, stages;
+};
+constexpr StreamVariant kStreamVariants[] = {{16, 4}, {8, 4}, {16, 3}, {8, 6}, {16, 6}};
+constexpr int kNumStreamVariants = sizeof(kStreamVariants) / sizeof(kStreamVariants[0]);
+
+template <int PPL, int STAGES, bool INT>
+cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
+{
+    using C = StreamCfg<PPL, STAGES>;
+    auto k = stream_tma_kernel<PPL, STAGES, INT>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStreamThreads, C::kSmem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int64_t tiles = (M + C::kTile - 1) / C::kTile;
+    const int blocks = (int)max((int64_t)1, min((int64_t)per_sm * t->num_sms, tiles));
+    k<<<blocks, kStreamThreads, C::kSmem, s>>>(t->d_poly, t->d_coef, t->d_g0, t->d_gk, t->d_verts,
+                                               t->vdtype, pts, M, mask, (StreamCounters *)t->d_stream_ctr,
+                                               t->d_qcount, t->d_error);
+    return cudaGetLastError();
+}
+
+template <int PPL, int STAGES>
+cudaError_t set_smem_attr()
+{
+    const int bytes = (int)StreamCfg<PPL, STAGES>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(stream_tma_kernel<PPL, STAGES, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stream_tma_kernel<PPL, STAGES, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+template <bool INT>
+cudaError_t launch_stream_tma(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask,
+                              cudaStream_t s)
+{
+    switch (t->stream_variant) {
+    case 1: return launch_tma_one<8, 4, INT>(t, pts, M, mask, s);
+    case 2: return launch_tma_one<16, 3, INT>(t, pts, M, mask, s);
+    case 3: return launch_tma_one<8, 6, INT>(t, pts, M, mask, s);
+    case 4: return launch_tma_one<16, 6, INT>(t, pts, M, mask, s);
+    default: return launch_tma_one<16, 4, INT>(t, pts, M, mask, s);
+    }
+}
+
 }  // namespace
+
+namespace pip {
+
+cudaError_t stream_kernels_setup()
+{
+    cudaError_t e = set_smem_attr<16, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<16, 3>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 6>();
+    if (e == cudaSuccess) e = set_smem_attr<16, 6>();
+    return e;
+}
+
+int stream_variant_count() { return kNumStreamVariants; }
+
+}  // namespace pip
 
 extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dtype pdtype,
                                int64_t num_points, const int64_t *d_point_offsets, int mode,
@@ -108,6 +174,15 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
                           : launch_ragged<true, false>(t, d_points, num_points, d_point_offsets, mask, s);
         else e = v16 ? launch_ragged<false, true>(t, d_points, num_points, d_point_offsets, mask, s)
                      : launch_ragged<false, false>(t, d_points, num_points, d_point_offsets, mask, s);
+    } else if (t->P == 1 && !want_hit && v16) {
+        // the pipelined kernel: bulk test and exact refine in one launch
+        timing_mark(t, 0, s);
+        e = ints ? launch_stream_tma<true>(t, d_points, num_points, mask, s)
+                 : launch_stream_tma<false>(t, d_points, num_points, mask, s);
+        if (e != cudaSuccess) return PIP_E_CUDA;
+        timing_mark(t, 1, s);
+        timing_mark(t, 2, s);
+        return PIP_OK;
     } else if (t->P == 1 && !want_hit) {
         kmode = kSingle;
         PIP_CUDA_TRY(cudaMemsetAsync(t->d_qcount, 0, sizeof(unsigned int), s));
@@ -147,5 +222,62 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     refine_kernel<<<t->num_sms * 2, kThreads, 0, s>>>(A, kmode);
     if (cudaGetLastError() != cudaSuccess) return PIP_E_CUDA;
     timing_mark(t, 2, s);
+    return PIP_OK;
+}
+
+extern "C" int32_t pip_stream_variant_count(void) { return kNumStreamVariants; }
+
+extern "C" pip_status pip_set_stream_variant(pip_tables *t, int32_t variant)
+{
+    pip_status st = check_tables(t);
+    if (st != PIP_OK) return st;
+    if (variant < 0 || variant >= kNumStreamVariants) return PIP_E_INVALID_ARG;
+    t->stream_variant = variant;
+    return PIP_OK;
+}
+
+extern "C" pip_status pip_autotune_stream(pip_tables *t, const void *d_points, pip_dtype pdtype,
+                                          int64_t num_points, uint32_t *d_mask, int32_t reps,
+                                          void *stream, int32_t *best_variant, float *best_ms)
+{
+    pip_status st = check_tables(t);
+    if (st != PIP_OK) return st;
+    if (t->P != 1 || num_points <= 0 || reps < 1 || !aligned(d_points, 16)) return PIP_E_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    PIP_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return PIP_E_CUDA;
+    }
+    const int keep = t->timing;
+    t->timing = 0;
+    int best = -1;
+    float best_t = 0.f;
+    pip_status out = PIP_OK;
+    for (int v = 0; v < kNumStreamVariants && out == PIP_OK; ++v) {
+        t->stream_variant = v;
+        out = pip_test(t, d_points, pdtype, num_points, nullptr, PIP_MASK, d_mask, nullptr, stream);
+        if (out != PIP_OK) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { out = PIP_E_CUDA; break; }
+        for (int r = 0; r < reps && out == PIP_OK; ++r)
+            out = pip_test(t, d_points, pdtype, num_points, nullptr, PIP_MASK, d_mask, nullptr, stream);
+        if (out != PIP_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            out = PIP_E_CUDA;
+            break;
+        }
+        ms /= reps;
+        if (best < 0 || ms < best_t) { best = v; best_t = ms; }
+    }
+    t->timing = keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out != PIP_OK) return out;
+    t->stream_variant = best;
+    if (best_variant) *best_variant = best;
+    if (best_ms) *best_ms = best_t;
     return PIP_OK;
 }
