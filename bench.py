@@ -184,6 +184,8 @@ def main():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--points", type=int, default=NUM_POINTS,
                     help="points of the workload (default the full 2^26; smaller only for profiling)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="tile shape of the pipelined kernel (default: autotuned)")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
                     help="warm up for at least this long so that clocks settle")
     args = ap.parse_args()
@@ -230,7 +232,11 @@ def main():
 
     stream = torch.cuda.current_stream()
     # tile shape of the pipelined kernel, tuned on this workload (not timed)
-    variant, variant_ms = B.pip_autotune_stream(t, p, mask, reps=5)
+    if args.variant >= 0:
+        variant = args.variant
+        B.pip_set_stream_variant(t, variant)
+    else:
+        variant, _ = B.pip_autotune_stream(t, p, mask, reps=5)
     clocks = ClockSampler(local)
     clocks.start()
     # warm-up: W steps, and at least 1 s of them so that clocks settle

@@ -82,7 +82,10 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     const size_t o_poly = take(P * sizeof(PolyInfo));
     const size_t o_items = take((P + 1) * sizeof(int64_t));
     const size_t o_cnt = take(128);
-    const size_t o_queue = take((size_t)(max_points > 0 ? max_points : 1) * sizeof(uint32_t));
+    // refine queue: every point once, plus the slack of the pipelined kernel's
+    // per-CTA slices (at most one tile of 4,096 points per CTA, 2 CTAs per SM)
+    const size_t queue_entries = (size_t)max_points + (size_t)(2 * t->num_sms + 1) * 4096;
+    const size_t o_queue = take(queue_entries * sizeof(uint32_t));
     t->bytes = off;
     if (cudaMalloc(&t->base, t->bytes) != cudaSuccess) {
         free(t);

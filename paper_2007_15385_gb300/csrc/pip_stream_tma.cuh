@@ -5,11 +5,13 @@
 // ring of shared-memory stages with 1-D bulk copies (cp.async.bulk), each
 // stage guarded by a "full" mbarrier (transaction bytes) and an "empty"
 // mbarrier (one arrive per consumer warp).  Consumer warps evaluate the
-// expanded Eq. 11 for two points at once with packed f32x2 FMAs, take the
-// "for all k" of Alg. 5 as a 3-input NaN-propagating min, and turn 32
-// decisions into one mask word with a ballot.  The few points whose float32
-// result lies within the error bound are decided exactly right there by the
-// whole warp (one lane per edge), so one launch does the whole test.
+// expanded Eq. 11, s_k = t_k - x w_kx - y w_ky, with two FMAs per edge and
+// take the "for all k" of Alg. 5 as a NaN-propagating running min; for up to
+// 16 edges the coefficients sit in registers (edge count a template
+// parameter), above that in shared memory.  32 decisions become one mask word
+// with a ballot.  The few points whose float32 result lies within the error
+// bound are decided exactly right there by the whole warp (one lane per
+// edge), so one launch does the whole test.
 #pragma once
 
 #include "pip_kernels.cuh"
@@ -104,28 +106,29 @@ struct StreamCfg {
     static constexpr int kTile = kConsumerWarps * 32 * PPL;  // points per stage
     static constexpr size_t kStageBytes = (size_t)kTile * 8;
     static constexpr size_t kCoefOff = STAGES * kStageBytes;
-    static constexpr int kCab = kMaxEdges + 2;       // float4 (-wx, -wx, -wy, -wy) per edge
-    static constexpr int kCtt = (kMaxEdges + 2) / 2; // float4 (t_k, t_k, t_k+1, t_k+1) per edge pair
-    static constexpr size_t kBarOff = kCoefOff + (size_t)(kCab + kCtt) * 16;
+    static constexpr int kCoef = kMaxEdges + 4;  // float4 (w_x, w_y, t, 0), padded to 4
+    static constexpr size_t kBarOff = kCoefOff + (size_t)kCoef * 16;
     static constexpr size_t kSmem = kBarOff + 2 * STAGES * sizeof(uint64_t);
-    // CTAs that fit one SM's 228 KB of shared memory (at most 3)
+    // two CTAs per SM (16 consumer warps, <= 112 registers a thread) when the
+    // shared memory allows it
     static constexpr int kFit = (int)((227 * 1024) / (kSmem + 1024));
-    static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 3 ? 3 : kFit);
+    static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
 };
 
-template <int PPL, int STAGES, bool INT>
+// NE > 0: the polygon has at most NE edges and the coefficients live in
+// registers; NE == 0: any edge count, coefficients read from shared memory.
+template <int NE, int PPL, int STAGES, bool INT>
 __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBlocks) stream_tma_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
     const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab,
     const void *__restrict__ verts, int vdtype, const void *__restrict__ pts, int64_t M,
-    uint32_t *__restrict__ mask, StreamCounters *__restrict__ ctr, unsigned int *__restrict__ last_refine,
-    int *__restrict__ err)
+    uint32_t *__restrict__ mask, uint32_t *__restrict__ queue, StreamCounters *__restrict__ ctr,
+    unsigned int *__restrict__ last_refine, int *__restrict__ err)
 {
     using C = StreamCfg<PPL, STAGES>;
     constexpr int kTile = C::kTile;
     extern __shared__ __align__(128) unsigned char smem[];
-    float4 *cab = (float4 *)(smem + C::kCoefOff);
-    float4 *ctt = cab + C::kCab;
+    float4 *cs = (float4 *)(smem + C::kCoefOff);
     uint64_t *full = (uint64_t *)(smem + C::kBarOff);
     uint64_t *empty = full + STAGES;
     __shared__ unsigned int s_refined;
@@ -134,15 +137,14 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
     const PolyInfo pi = poly[0];
     const bool ok = pi.status == PIP_OK;
     const int n = ok ? pi.n : 1;
-    const int npad = (n + 1) & ~1;
+    const int npad = (n + 3) & ~3;
+    // edges past n never win the min (w = 0, t = +inf); an invalid polygon is
+    // one edge with t = -inf and contains nothing
     for (int k = tid; k < npad; k += blockDim.x) {
         float4 c;
         if (!ok) c = k == 0 ? make_float4(0.f, 0.f, -INFINITY, 0.f) : make_float4(0.f, 0.f, INFINITY, 0.f);
         else c = k < n ? coef[pi.voff + k] : make_float4(0.f, 0.f, INFINITY, 0.f);
-        cab[k] = make_float4(-c.x, -c.x, -c.y, -c.y);
-        float *tt = (float *)ctt;
-        tt[2 * k] = c.z;
-        tt[2 * k + 1] = c.z;
+        cs[k] = c;
     }
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -156,6 +158,9 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
 
     const int64_t ntiles = (M + kTile - 1) / kTile;
     const int64_t mine = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    // this CTA's slice of the scratch queue: room for every point it owns
+    const int64_t per_cta = ((ntiles + gridDim.x - 1) / gridDim.x) * kTile;
+    uint32_t *myqueue = queue + (int64_t)blockIdx.x * per_cta;
 
     if (warp == kConsumerWarps) {
         // ---------------- producer: one elected lane issues the bulk copies
@@ -182,11 +187,18 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
         }
     } else {
         // ---------------- consumers
-        const float ox = pi.ox, oy = pi.oy;
-        const f2x NOX = pk(-ox, -ox), NOY = pk(-oy, -oy);
-        const f2x B0P = pk(pi.beta0, pi.beta0), B1P = pk(pi.beta1, pi.beta1);
+        const float ox = pi.ox, oy = pi.oy, b0 = pi.beta0, b1 = pi.beta1;
+        float cwx[NE > 0 ? NE : 1], cwy[NE > 0 ? NE : 1], ct[NE > 0 ? NE : 1];
+        if (NE > 0) {
+#pragma unroll
+            for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
+                const float4 c = k < npad ? cs[k] : make_float4(0.f, 0.f, INFINITY, 0.f);
+                cwx[k] = c.x;
+                cwy[k] = c.y;
+                ct[k] = c.z;
+            }
+        }
         const int64_t nwords = (M + 31) >> 5;
-        unsigned int refined = 0;
         for (int64_t it = 0; it < mine; ++it) {
             const int s = (int)(it % STAGES);
             if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), err)) break;
@@ -199,8 +211,18 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
             for (int q = 0; q < PPL; ++q) {
                 const int64_t p = wfirst + 32 * q + lane;
                 float x = 0.f, y = 0.f;
-                if (!tail || p < M) {
-                    if (tail && p == M - 1 && (M & 1)) {
+                if (!tail) {
+                    if (INT) {
+                        const int2 v = ((const int2 *)stage)[32 * q + lane];
+                        x = (float)v.x;
+                        y = (float)v.y;
+                    } else {
+                        const float2 v = ((const float2 *)stage)[32 * q + lane];
+                        x = v.x;
+                        y = v.y;
+                    }
+                } else if (p < M) {
+                    if (p == M - 1 && (M & 1)) {
                         // the odd last point is not in the bulk copy
                         if (INT) {
                             x = (float)((const int32_t *)pts)[2 * p];
@@ -222,67 +244,61 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                 px[q] = x;
                 py[q] = y;
             }
-            f2x X[PPL / 2], Y[PPL / 2];
-            float m[PPL];
+            float xs[PPL], ys[PPL], m[PPL];
 #pragma unroll
-            for (int i = 0; i < PPL / 2; ++i) {
-                X[i] = fadd2(pk(px[2 * i], px[2 * i + 1]), NOX);  // x - o, rounded as in fl(x - o)
-                Y[i] = fadd2(pk(py[2 * i], py[2 * i + 1]), NOY);
-                m[2 * i] = INFINITY;
-                m[2 * i + 1] = INFINITY;
+            for (int q = 0; q < PPL; ++q) {
+                xs[q] = px[q] - ox;  // local coordinates x = p - o
+                ys[q] = py[q] - oy;
             }
-            for (int e = 0; e < npad; e += 2) {
-                const float4 a0 = cab[e], a1 = cab[e + 1], tt = ctt[e >> 1];
-                const f2x A0 = pk(a0.x, a0.y), Bw0 = pk(a0.z, a0.w);
-                const f2x A1 = pk(a1.x, a1.y), Bw1 = pk(a1.z, a1.w);
-                const f2x T0 = pk(tt.x, tt.y), T1 = pk(tt.z, tt.w);
+            if (NE > 0) {
 #pragma unroll
-                for (int i = 0; i < PPL / 2; ++i) {
-                    // s_k = t_k - x w_kx - y w_ky for the two points of the pair
-                    const f2x s0 = ffma2(X[i], A0, ffma2(Y[i], Bw0, T0));
-                    const f2x s1 = ffma2(X[i], A1, ffma2(Y[i], Bw1, T1));
-                    float s0l, s0h, s1l, s1h;
-                    upk(s0, s0l, s0h);
-                    upk(s1, s1l, s1h);
-                    m[2 * i] = fmin3_nan(m[2 * i], s0l, s1l);
-                    m[2 * i + 1] = fmin3_nan(m[2 * i + 1], s0h, s1h);
+                for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        const float sk = fmaf(-xs[q], cwx[k], fmaf(-ys[q], cwy[k], ct[k]));
+                        m[q] = k == 0 ? sk : fmin_nan(m[q], sk);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) m[q] = INFINITY;
+                for (int k = 0; k < npad; k += 4) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const float4 c = cs[k + kk];
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q)
+                            m[q] = fmin_nan(m[q], fmaf(-xs[q], c.x, fmaf(-ys[q], c.y, c.z)));
+                    }
                 }
             }
-            // decisions: one ballot per 32 points for "inside", one for "uncertain"
-            uint32_t w_in[PPL], w_unc[PPL];
-            uint32_t any_unc = 0;
+            // decisions: one ballot per 32 points for "inside", one vote per
+            // stage slice for "anything uncertain"
+            uint32_t w_in[PPL];
+            bool unc[PPL];
+            bool any = false;
 #pragma unroll
-            for (int i = 0; i < PPL / 2; ++i) {
-                float x0, x1, y0, y1;
-                upk(X[i], x0, x1);
-                upk(Y[i], y0, y1);
-                const f2x N = pk(fmaxf(fabsf(x0), fabsf(y0)), fmaxf(fabsf(x1), fabsf(y1)));
-                float B[2];
-                upk(ffma2(N, B1P, B0P), B[0], B[1]);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int q = 2 * i + h;
-                    const bool valid = !tail || wfirst + 32 * q + lane < M;
-                    bool in = m[q] >= B[h];
-                    bool unc = !(fabsf(m[q]) >= B[h]);
-                    if (INT && !int_exact(px[q], py[q])) { in = false; unc = true; }
-                    w_in[q] = __ballot_sync(0xffffffffu, in && valid);
-                    w_unc[q] = __ballot_sync(0xffffffffu, unc && valid);
-                    any_unc |= w_unc[q];
-                }
+            for (int q = 0; q < PPL; ++q) {
+                const float B = fmaf(b1, fmaxf(fabsf(xs[q]), fabsf(ys[q])), b0);
+                const bool valid = !tail || wfirst + 32 * q + lane < M;
+                bool in = m[q] >= B;
+                bool u = !(fabsf(m[q]) >= B);
+                if (INT && !int_exact(px[q], py[q])) { in = false; u = true; }
+                unc[q] = u && valid;
+                any |= unc[q];
+                w_in[q] = __ballot_sync(0xffffffffu, in && valid);
             }
-            if (any_unc) {
-                // rare: the whole warp decides each uncertain point exactly
+            if (__any_sync(0xffffffffu, any)) {
+                // rare: queue the uncertain points; they are decided after the
+                // tile loop, when the coefficient registers are free
 #pragma unroll
                 for (int q = 0; q < PPL; ++q) {
-                    uint32_t u = w_unc[q];
-                    while (u) {
-                        const int l = __ffs(u) - 1;
-                        u &= u - 1;
-                        if (warp_inside_exact(poly, 0, g0tab, gktab, verts, vdtype, pts,
-                                              INT ? PIP_I32 : PIP_F32, wfirst + 32 * q + l))
-                            w_in[q] |= 1u << l;
-                        ++refined;
+                    const uint32_t u = __ballot_sync(0xffffffffu, unc[q]);
+                    if (u) {
+                        unsigned int base = 0;
+                        if (lane == 0) base = atomicAdd(&s_refined, (unsigned int)__popc(u));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (unc[q]) myqueue[base + __popc(u & ((1u << lane) - 1u))] = (uint32_t)(wfirst + 32 * q + lane);
                     }
                 }
             }
@@ -294,9 +310,18 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
-        if (lane == 0 && refined) atomicAdd(&s_refined, refined);
     }
     __syncthreads();
+    // exact decision of this CTA's queued points, one warp per point (every
+    // warp of the CTA, the producer's included); their mask words were
+    // written above with the bit clear
+    const unsigned int nq = s_refined;
+    for (unsigned int i = warp; i < nq; i += kConsumerWarps + 1) {
+        const int64_t p = myqueue[i];
+        if (warp_inside_exact(poly, 0, g0tab, gktab, verts, vdtype, pts, INT ? PIP_I32 : PIP_F32, p) &&
+            lane == 0)
+            atomicOr(&mask[p >> 5], 1u << (p & 31));
+    }
     if (tid == 0) {
         if (s_refined) atomicAdd(&ctr->refine, s_refined);
         __threadfence();

@@ -68,35 +68,59 @@ cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int
 struct StreamVariant {
     int ppl, stages;
 };
-constexpr StreamVariant kStreamVariants[] = {{16, 4}, {8, 4}, {16, 3}, {8, 6}, {16, 6}};
+constexpr StreamVariant kStreamVariants[] = {{8, 4}, {8, 3}, {16, 2}, {4, 6}};
 constexpr int kNumStreamVariants = sizeof(kStreamVariants) / sizeof(kStreamVariants[0]);
 
-template <int PPL, int STAGES, bool INT>
+template <int NE, int PPL, int STAGES, bool INT>
 cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
 {
     using C = StreamCfg<PPL, STAGES>;
-    auto k = stream_tma_kernel<PPL, STAGES, INT>;
+    auto k = stream_tma_kernel<NE, PPL, STAGES, INT>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStreamThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
+    if (per_sm > 2) per_sm = 2;  // the scratch queue holds one tile of slack per CTA, 2 CTAs per SM
     const int64_t tiles = (M + C::kTile - 1) / C::kTile;
     const int blocks = (int)max((int64_t)1, min((int64_t)per_sm * t->num_sms, tiles));
     k<<<blocks, kStreamThreads, C::kSmem, s>>>(t->d_poly, t->d_coef, t->d_g0, t->d_gk, t->d_verts,
-                                               t->vdtype, pts, M, mask, (StreamCounters *)t->d_stream_ctr,
-                                               t->d_qcount, t->d_error);
+                                               t->vdtype, pts, M, mask, t->d_queue,
+                                               (StreamCounters *)t->d_stream_ctr, t->d_qcount, t->d_error);
     return cudaGetLastError();
+}
+
+template <int PPL, int STAGES, bool INT>
+cudaError_t launch_tma_ne(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
+{
+    // the polygon's edge count is known on the host from the vertex count
+    const int n = t->V;
+    if (n <= 4) return launch_tma_one<4, PPL, STAGES, INT>(t, pts, M, mask, s);
+    if (n <= 8) return launch_tma_one<8, PPL, STAGES, INT>(t, pts, M, mask, s);
+    if (n <= 12) return launch_tma_one<12, PPL, STAGES, INT>(t, pts, M, mask, s);
+    if (n <= 16) return launch_tma_one<16, PPL, STAGES, INT>(t, pts, M, mask, s);
+    return launch_tma_one<0, PPL, STAGES, INT>(t, pts, M, mask, s);
+}
+
+template <int NE, int PPL, int STAGES>
+cudaError_t set_attr_one()
+{
+    const int bytes = (int)StreamCfg<PPL, STAGES>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 template <int PPL, int STAGES>
 cudaError_t set_smem_attr()
 {
-    const int bytes = (int)StreamCfg<PPL, STAGES>::kSmem;
-    cudaError_t e = cudaFuncSetAttribute(stream_tma_kernel<PPL, STAGES, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(stream_tma_kernel<PPL, STAGES, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = set_attr_one<4, PPL, STAGES>();
+    if (e == cudaSuccess) e = set_attr_one<8, PPL, STAGES>();
+    if (e == cudaSuccess) e = set_attr_one<12, PPL, STAGES>();
+    if (e == cudaSuccess) e = set_attr_one<16, PPL, STAGES>();
+    if (e == cudaSuccess) e = set_attr_one<0, PPL, STAGES>();
     return e;
 }
 
@@ -105,11 +129,10 @@ cudaError_t launch_stream_tma(const pip_tables *t, const void *pts, int64_t M, u
                               cudaStream_t s)
 {
     switch (t->stream_variant) {
-    case 1: return launch_tma_one<8, 4, INT>(t, pts, M, mask, s);
-    case 2: return launch_tma_one<16, 3, INT>(t, pts, M, mask, s);
-    case 3: return launch_tma_one<8, 6, INT>(t, pts, M, mask, s);
-    case 4: return launch_tma_one<16, 6, INT>(t, pts, M, mask, s);
-    default: return launch_tma_one<16, 4, INT>(t, pts, M, mask, s);
+    case 1: return launch_tma_ne<8, 3, INT>(t, pts, M, mask, s);
+    case 2: return launch_tma_ne<16, 2, INT>(t, pts, M, mask, s);
+    case 3: return launch_tma_ne<4, 6, INT>(t, pts, M, mask, s);
+    default: return launch_tma_ne<8, 4, INT>(t, pts, M, mask, s);
     }
 }
 
@@ -119,11 +142,10 @@ namespace pip {
 
 cudaError_t stream_kernels_setup()
 {
-    cudaError_t e = set_smem_attr<16, 4>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 4>();
-    if (e == cudaSuccess) e = set_smem_attr<16, 3>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 6>();
-    if (e == cudaSuccess) e = set_smem_attr<16, 6>();
+    cudaError_t e = set_smem_attr<8, 4>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 3>();
+    if (e == cudaSuccess) e = set_smem_attr<16, 2>();
+    if (e == cudaSuccess) e = set_smem_attr<4, 6>();
     return e;
 }
 

@@ -110,6 +110,14 @@ __device__ __forceinline__ f2x fadd2(f2x a, f2x b)
     return d;
 }
 
+// min of two; NaN if either operand is NaN (full issue rate on sm_103)
+__device__ __forceinline__ float fmin_nan(float a, float b)
+{
+    float d;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 // min of three; NaN if any operand is NaN
 __device__ __forceinline__ float fmin3_nan(float a, float b, float c)
 {
