@@ -198,20 +198,21 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                 ct[k] = c.z;
             }
         }
-        const int64_t nwords = (M + 31) >> 5;
+        const bool vec_store = ((uintptr_t)mask & 15) == 0;
         for (int64_t it = 0; it < mine; ++it) {
             const int s = (int)(it % STAGES);
             if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), err)) break;
             const int64_t first = ((int64_t)blockIdx.x + it * gridDim.x) * kTile;
             const int64_t wfirst = first + warp * 32 * PPL;
-            const bool tail = first + kTile > M;
             const unsigned char *stage = smem + (size_t)s * C::kStageBytes + (size_t)warp * 32 * PPL * 8;
-            float px[PPL], py[PPL];
+            // points of this warp's slice that exist (all of them except in the last tile)
+            const int nvalid = (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst));
+            float xs[PPL], ys[PPL], m[PPL];
+            bool exin[PPL];
+            if (nvalid == 32 * PPL && !((M & 1) && wfirst + 32 * PPL == M)) {
 #pragma unroll
-            for (int q = 0; q < PPL; ++q) {
-                const int64_t p = wfirst + 32 * q + lane;
-                float x = 0.f, y = 0.f;
-                if (!tail) {
+                for (int q = 0; q < PPL; ++q) {
+                    float x, y;
                     if (INT) {
                         const int2 v = ((const int2 *)stage)[32 * q + lane];
                         x = (float)v.x;
@@ -221,34 +222,41 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                         x = v.x;
                         y = v.y;
                     }
-                } else if (p < M) {
-                    if (p == M - 1 && (M & 1)) {
-                        // the odd last point is not in the bulk copy
-                        if (INT) {
-                            x = (float)((const int32_t *)pts)[2 * p];
-                            y = (float)((const int32_t *)pts)[2 * p + 1];
-                        } else {
-                            x = ((const float *)pts)[2 * p];
-                            y = ((const float *)pts)[2 * p + 1];
-                        }
-                    } else if (INT) {
-                        const int2 v = ((const int2 *)stage)[32 * q + lane];
-                        x = (float)v.x;
-                        y = (float)v.y;
-                    } else {
-                        const float2 v = ((const float2 *)stage)[32 * q + lane];
-                        x = v.x;
-                        y = v.y;
-                    }
+                    exin[q] = INT ? int_exact(x, y) : true;
+                    xs[q] = x - ox;  // local coordinates x = p - o
+                    ys[q] = y - oy;
                 }
-                px[q] = x;
-                py[q] = y;
-            }
-            float xs[PPL], ys[PPL], m[PPL];
+            } else {
+                // the last tile: points past M are set to the origin and masked
+                // below; an odd last point is not in the bulk copy
 #pragma unroll
-            for (int q = 0; q < PPL; ++q) {
-                xs[q] = px[q] - ox;  // local coordinates x = p - o
-                ys[q] = py[q] - oy;
+                for (int q = 0; q < PPL; ++q) {
+                    const int r = 32 * q + lane;
+                    float x = ox, y = oy;
+                    if (r < nvalid) {
+                        const int64_t p = wfirst + r;
+                        if (p == M - 1 && (M & 1)) {
+                            if (INT) {
+                                x = (float)((const int32_t *)pts)[2 * p];
+                                y = (float)((const int32_t *)pts)[2 * p + 1];
+                            } else {
+                                x = ((const float *)pts)[2 * p];
+                                y = ((const float *)pts)[2 * p + 1];
+                            }
+                        } else if (INT) {
+                            const int2 v = ((const int2 *)stage)[r];
+                            x = (float)v.x;
+                            y = (float)v.y;
+                        } else {
+                            const float2 v = ((const float2 *)stage)[r];
+                            x = v.x;
+                            y = v.y;
+                        }
+                    }
+                    exin[q] = INT ? int_exact(x, y) : true;
+                    xs[q] = x - ox;
+                    ys[q] = y - oy;
+                }
             }
             if (NE > 0) {
 #pragma unroll
@@ -273,20 +281,18 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                 }
             }
             // decisions: one ballot per 32 points for "inside", one vote per
-            // stage slice for "anything uncertain"
+            // slice for "anything uncertain"
             uint32_t w_in[PPL];
             bool unc[PPL];
             bool any = false;
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
                 const float B = fmaf(b1, fmaxf(fabsf(xs[q]), fabsf(ys[q])), b0);
-                const bool valid = !tail || wfirst + 32 * q + lane < M;
-                bool in = m[q] >= B;
-                bool u = !(fabsf(m[q]) >= B);
-                if (INT && !int_exact(px[q], py[q])) { in = false; u = true; }
-                unc[q] = u && valid;
+                const bool valid = 32 * q + lane < nvalid;
+                const bool in = (m[q] >= B) && exin[q] && valid;
+                unc[q] = (!(fabsf(m[q]) >= B) || !exin[q]) && valid;
                 any |= unc[q];
-                w_in[q] = __ballot_sync(0xffffffffu, in && valid);
+                w_in[q] = __ballot_sync(0xffffffffu, in);
             }
             if (__any_sync(0xffffffffu, any)) {
                 // rare: queue the uncertain points; they are decided after the
@@ -302,11 +308,22 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                     }
                 }
             }
-            uint32_t myword = 0;
+            // the slice's mask words: PPL consecutive words
+            const int nw = (nvalid + 31) >> 5;
+            uint32_t *mw = mask + (wfirst >> 5);
+            if (vec_store && nw == PPL && (PPL % 4) == 0) {
+                if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < PPL; ++q)
-                if (lane == q) myword = w_in[q];
-            if (lane < PPL && (wfirst >> 5) + lane < nwords) mask[(wfirst >> 5) + lane] = myword;
+                    for (int q = 0; q < PPL; q += 4)
+                        *(uint4 *)(mw + q) = make_uint4(w_in[q], w_in[q + 1], w_in[q + 2], w_in[q + 3]);
+                }
+            } else {
+                uint32_t myword = 0;
+#pragma unroll
+                for (int q = 0; q < PPL; ++q)
+                    if (lane == q) myword = w_in[q];
+                if (lane < nw) mw[lane] = myword;
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
