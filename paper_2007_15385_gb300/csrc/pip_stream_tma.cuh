@@ -117,7 +117,8 @@ struct StreamCfg {
 
 // NE > 0: the polygon has at most NE edges and the coefficients live in
 // registers; NE == 0: any edge count, coefficients read from shared memory.
-template <int NE, int PPL, int STAGES, bool INT>
+// MIN3: take the running min three operands at a time.
+template <int NE, int PPL, int STAGES, bool INT, bool MIN3>
 __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBlocks) stream_tma_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
     const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab,
@@ -258,13 +259,33 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                     ys[q] = y - oy;
                 }
             }
+            // m = min_k s_k.  The min ignores a NaN operand, so a point with a
+            // non-finite coordinate is caught by its bound below instead.
             if (NE > 0) {
-#pragma unroll
-                for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
+                if (MIN3 && NE >= 3) {
 #pragma unroll
                     for (int q = 0; q < PPL; ++q) {
-                        const float sk = fmaf(-xs[q], cwx[k], fmaf(-ys[q], cwy[k], ct[k]));
-                        m[q] = k == 0 ? sk : fmin_nan(m[q], sk);
+                        float acc = fmaf(-xs[q], cwx[0], fmaf(-ys[q], cwy[0], ct[0]));
+#pragma unroll
+                        for (int k = 1; k + 1 < (NE > 0 ? NE : 1); k += 2) {
+                            const float s1 = fmaf(-xs[q], cwx[k], fmaf(-ys[q], cwy[k], ct[k]));
+                            const float s2 = fmaf(-xs[q], cwx[k + 1], fmaf(-ys[q], cwy[k + 1], ct[k + 1]));
+                            acc = fmin3(acc, s1, s2);
+                        }
+                        if ((NE & 1) == 0) {
+                            const int k = (NE > 0 ? NE : 1) - 1;
+                            acc = fminf(acc, fmaf(-xs[q], cwx[k], fmaf(-ys[q], cwy[k], ct[k])));
+                        }
+                        m[q] = acc;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) {
+                            const float sk = fmaf(-xs[q], cwx[k], fmaf(-ys[q], cwy[k], ct[k]));
+                            m[q] = k == 0 ? sk : fminf(m[q], sk);
+                        }
                     }
                 }
             } else {
@@ -276,7 +297,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                         const float4 c = cs[k + kk];
 #pragma unroll
                         for (int q = 0; q < PPL; ++q)
-                            m[q] = fmin_nan(m[q], fmaf(-xs[q], c.x, fmaf(-ys[q], c.y, c.z)));
+                            m[q] = fminf(m[q], fmaf(-xs[q], c.x, fmaf(-ys[q], c.y, c.z)));
                     }
                 }
             }
@@ -287,10 +308,14 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
             bool any = false;
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
-                const float B = fmaf(b1, fmaxf(fabsf(xs[q]), fabsf(ys[q])), b0);
+                // B >= beta0 + beta1 max(|x|, |y|); |x| + |y| also turns a NaN
+                // or infinite coordinate into a B that is not finite, and such
+                // points are never decided here
+                const float B = fmaf(b1, fabsf(xs[q]) + fabsf(ys[q]), b0);
                 const bool valid = 32 * q + lane < nvalid;
-                const bool in = (m[q] >= B) && exin[q] && valid;
-                unc[q] = (!(fabsf(m[q]) >= B) || !exin[q]) && valid;
+                const bool fin = B < INFINITY;
+                const bool in = (m[q] >= B) && fin && exin[q] && valid;
+                unc[q] = (!(fabsf(m[q]) >= B) || !fin || !exin[q]) && valid;
                 any |= unc[q];
                 w_in[q] = __ballot_sync(0xffffffffu, in);
             }

@@ -64,18 +64,19 @@ cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int
     return cudaGetLastError();
 }
 
-// Tile shapes of the pipelined kernel: (points per lane per stage, stages).
+// Variants of the pipelined kernel: (points per lane per stage, stages,
+// 3-operand min).
 struct StreamVariant {
-    int ppl, stages;
+    int ppl, stages, min3;
 };
-constexpr StreamVariant kStreamVariants[] = {{8, 4}, {8, 3}, {16, 2}, {4, 6}};
+constexpr StreamVariant kStreamVariants[] = {{8, 4, 0}, {8, 4, 1}, {8, 3, 0}, {16, 2, 0}};
 constexpr int kNumStreamVariants = sizeof(kStreamVariants) / sizeof(kStreamVariants[0]);
 
-template <int NE, int PPL, int STAGES, bool INT>
+template <int NE, int PPL, int STAGES, bool INT, bool MIN3>
 cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
 {
     using C = StreamCfg<PPL, STAGES>;
-    auto k = stream_tma_kernel<NE, PPL, STAGES, INT>;
+    auto k = stream_tma_kernel<NE, PPL, STAGES, INT, MIN3>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStreamThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
@@ -89,38 +90,38 @@ cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint
     return cudaGetLastError();
 }
 
-template <int PPL, int STAGES, bool INT>
+template <int PPL, int STAGES, bool INT, bool MIN3>
 cudaError_t launch_tma_ne(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
 {
     // the polygon's edge count is known on the host from the vertex count
     const int n = t->V;
-    if (n <= 4) return launch_tma_one<4, PPL, STAGES, INT>(t, pts, M, mask, s);
-    if (n <= 8) return launch_tma_one<8, PPL, STAGES, INT>(t, pts, M, mask, s);
-    if (n <= 12) return launch_tma_one<12, PPL, STAGES, INT>(t, pts, M, mask, s);
-    if (n <= 16) return launch_tma_one<16, PPL, STAGES, INT>(t, pts, M, mask, s);
-    return launch_tma_one<0, PPL, STAGES, INT>(t, pts, M, mask, s);
+    if (n <= 4) return launch_tma_one<4, PPL, STAGES, INT, MIN3>(t, pts, M, mask, s);
+    if (n <= 8) return launch_tma_one<8, PPL, STAGES, INT, MIN3>(t, pts, M, mask, s);
+    if (n <= 12) return launch_tma_one<12, PPL, STAGES, INT, MIN3>(t, pts, M, mask, s);
+    if (n <= 16) return launch_tma_one<16, PPL, STAGES, INT, MIN3>(t, pts, M, mask, s);
+    return launch_tma_one<0, PPL, STAGES, INT, MIN3>(t, pts, M, mask, s);
 }
 
-template <int NE, int PPL, int STAGES>
+template <int NE, int PPL, int STAGES, bool MIN3>
 cudaError_t set_attr_one()
 {
     const int bytes = (int)StreamCfg<PPL, STAGES>::kSmem;
-    cudaError_t e = cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, false>,
+    cudaError_t e = cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, false, MIN3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, true>,
+        e = cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, true, MIN3>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
-template <int PPL, int STAGES>
+template <int PPL, int STAGES, bool MIN3>
 cudaError_t set_smem_attr()
 {
-    cudaError_t e = set_attr_one<4, PPL, STAGES>();
-    if (e == cudaSuccess) e = set_attr_one<8, PPL, STAGES>();
-    if (e == cudaSuccess) e = set_attr_one<12, PPL, STAGES>();
-    if (e == cudaSuccess) e = set_attr_one<16, PPL, STAGES>();
-    if (e == cudaSuccess) e = set_attr_one<0, PPL, STAGES>();
+    cudaError_t e = set_attr_one<4, PPL, STAGES, MIN3>();
+    if (e == cudaSuccess) e = set_attr_one<8, PPL, STAGES, MIN3>();
+    if (e == cudaSuccess) e = set_attr_one<12, PPL, STAGES, MIN3>();
+    if (e == cudaSuccess) e = set_attr_one<16, PPL, STAGES, MIN3>();
+    if (e == cudaSuccess) e = set_attr_one<0, PPL, STAGES, MIN3>();
     return e;
 }
 
@@ -129,10 +130,10 @@ cudaError_t launch_stream_tma(const pip_tables *t, const void *pts, int64_t M, u
                               cudaStream_t s)
 {
     switch (t->stream_variant) {
-    case 1: return launch_tma_ne<8, 3, INT>(t, pts, M, mask, s);
-    case 2: return launch_tma_ne<16, 2, INT>(t, pts, M, mask, s);
-    case 3: return launch_tma_ne<4, 6, INT>(t, pts, M, mask, s);
-    default: return launch_tma_ne<8, 4, INT>(t, pts, M, mask, s);
+    case 1: return launch_tma_ne<8, 4, INT, true>(t, pts, M, mask, s);
+    case 2: return launch_tma_ne<8, 3, INT, false>(t, pts, M, mask, s);
+    case 3: return launch_tma_ne<16, 2, INT, false>(t, pts, M, mask, s);
+    default: return launch_tma_ne<8, 4, INT, false>(t, pts, M, mask, s);
     }
 }
 
@@ -142,10 +143,10 @@ namespace pip {
 
 cudaError_t stream_kernels_setup()
 {
-    cudaError_t e = set_smem_attr<8, 4>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 3>();
-    if (e == cudaSuccess) e = set_smem_attr<16, 2>();
-    if (e == cudaSuccess) e = set_smem_attr<4, 6>();
+    cudaError_t e = set_smem_attr<8, 4, false>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 4, true>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 3, false>();
+    if (e == cudaSuccess) e = set_smem_attr<16, 2, false>();
     return e;
 }
 
