@@ -197,9 +197,12 @@ __global__ void __launch_bounds__(256) prepare_kernel(
         return;
     }
 
-    // local origin o = float32(p0), and o relative to the shift
+    // local origin o = float32(p0), and o relative to the shift; when the
+    // centroid is no farther from (0, 0) than the polygon's own extent, o is
+    // (0, 0) itself and the kernels skip the subtraction
     const double g0ax = g0x + sx, g0ay = g0y + sy;
-    const float ox = (float)g0ax, oy = (float)g0ay;
+    const bool at_zero = fmax(fabs(g0ax), fabs(g0ay)) <= D;
+    const float ox = at_zero ? 0.f : (float)g0ax, oy = at_zero ? 0.f : (float)g0ay;
     const double olx = (double)ox - sx, oly = (double)oy - sy;
 
     float tmax = 0.f, w1 = 0.f;

@@ -115,6 +115,123 @@ struct StreamCfg {
     static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
 };
 
+template <int NE>
+struct SliceCtx {
+    float ox, oy, b0, b1;
+    const float *cwx, *cwy, *ct;  // register-resident coefficients (NE > 0)
+    const float4 *cs;             // shared-memory coefficients (NE == 0)
+    int npad;
+};
+
+// One consumer warp, one slice of 32 * PPL points of a stage: evaluate, write
+// the slice's PPL mask words, queue the uncertain points.  TAIL: the slice may
+// run past M (or hold the odd last point, which is not in the bulk copy).
+// CENTER: subtract the local origin o (false when o = (0, 0)).
+template <int NE, int PPL, bool INT, bool MIN3, bool CENTER, bool TAIL>
+__device__ __forceinline__ void consume_slice(const SliceCtx<NE> &cx, const unsigned char *stage,
+                                              const void *__restrict__ pts, int64_t M, int64_t wfirst,
+                                              int lane, uint32_t *__restrict__ mask, bool vec_store,
+                                              uint32_t *__restrict__ myqueue, unsigned int *s_queued)
+{
+    const int nvalid = TAIL ? (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst)) : 32 * PPL;
+    float xs[PPL], ys[PPL], m[PPL];
+    bool exin[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        const int r = 32 * q + lane;
+        float x = cx.ox, y = cx.oy;
+        if (!TAIL || r < nvalid) {
+            if (TAIL && wfirst + r == M - 1 && (M & 1)) {
+                const int64_t p = M - 1;
+                if (INT) {
+                    x = (float)((const int32_t *)pts)[2 * p];
+                    y = (float)((const int32_t *)pts)[2 * p + 1];
+                } else {
+                    x = ((const float *)pts)[2 * p];
+                    y = ((const float *)pts)[2 * p + 1];
+                }
+            } else if (INT) {
+                const int2 v = ((const int2 *)stage)[r];
+                x = (float)v.x;
+                y = (float)v.y;
+            } else {
+                const float2 v = ((const float2 *)stage)[r];
+                x = v.x;
+                y = v.y;
+            }
+        }
+        exin[q] = INT ? int_exact(x, y) : true;
+        xs[q] = CENTER ? x - cx.ox : x;  // local coordinates x = p - o
+        ys[q] = CENTER ? y - cx.oy : y;
+    }
+    // m = min_k s_k, NaN-propagating so that a non-finite point stays undecided
+    if (NE > 0) {
+#pragma unroll
+        for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                const float sk = fmaf(-xs[q], cx.cwx[k], fmaf(-ys[q], cx.cwy[k], cx.ct[k]));
+                m[q] = k == 0 ? sk : fmin_nan(m[q], sk);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) m[q] = INFINITY;
+        for (int k = 0; k < cx.npad; k += 4) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float4 c = cx.cs[k + kk];
+#pragma unroll
+                for (int q = 0; q < PPL; ++q)
+                    m[q] = fmin_nan(m[q], fmaf(-xs[q], c.x, fmaf(-ys[q], c.y, c.z)));
+            }
+        }
+    }
+    // decisions: one ballot per 32 points for "inside", one vote for the slice
+    uint32_t w_in[PPL];
+    bool unc[PPL];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        const float B = fmaf(cx.b1, fmaxf(fabsf(xs[q]), fabsf(ys[q])), cx.b0);
+        const bool valid = !TAIL || 32 * q + lane < nvalid;
+        const bool in = (m[q] >= B) && (!INT || exin[q]) && valid;
+        unc[q] = (!(fabsf(m[q]) >= B) || (INT && !exin[q])) && valid;
+        any |= unc[q];
+        w_in[q] = __ballot_sync(0xffffffffu, in);
+    }
+    if (__any_sync(0xffffffffu, any)) {
+        // rare: queue the uncertain points; they are decided after the tile
+        // loop, when the coefficient registers are free
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            const uint32_t u = __ballot_sync(0xffffffffu, unc[q]);
+            if (u) {
+                unsigned int base = 0;
+                if (lane == 0) base = atomicAdd(s_queued, (unsigned int)__popc(u));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (unc[q]) myqueue[base + __popc(u & ((1u << lane) - 1u))] = (uint32_t)(wfirst + 32 * q + lane);
+            }
+        }
+    }
+    // the slice's mask words: PPL consecutive words
+    uint32_t *mw = mask + (wfirst >> 5);
+    if (!TAIL && vec_store && (PPL % 4) == 0) {
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < PPL; q += 4)
+                *(uint4 *)(mw + q) = make_uint4(w_in[q], w_in[q + 1], w_in[q + 2], w_in[q + 3]);
+        }
+    } else {
+        const int nw = (nvalid + 31) >> 5;
+        uint32_t myword = 0;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            if (lane == q) myword = w_in[q];
+        if (lane < nw) mw[lane] = myword;
+    }
+}
+
 // NE > 0: the polygon has at most NE edges and the coefficients live in
 // registers; NE == 0: any edge count, coefficients read from shared memory.
 // MIN3: take the running min three operands at a time.
@@ -189,6 +306,8 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
     } else {
         // ---------------- consumers
         const float ox = pi.ox, oy = pi.oy, b0 = pi.beta0, b1 = pi.beta1;
+        // o = (0, 0) when prepare chose the origin itself: no centring needed
+        const bool center = !(ox == 0.f && oy == 0.f);
         float cwx[NE > 0 ? NE : 1], cwy[NE > 0 ? NE : 1], ct[NE > 0 ? NE : 1];
         if (NE > 0) {
 #pragma unroll
@@ -200,154 +319,24 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
             }
         }
         const bool vec_store = ((uintptr_t)mask & 15) == 0;
+        SliceCtx<NE> cx{ox, oy, b0, b1, cwx, cwy, ct, cs, npad};
         for (int64_t it = 0; it < mine; ++it) {
             const int s = (int)(it % STAGES);
             if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), err)) break;
             const int64_t first = ((int64_t)blockIdx.x + it * gridDim.x) * kTile;
             const int64_t wfirst = first + warp * 32 * PPL;
             const unsigned char *stage = smem + (size_t)s * C::kStageBytes + (size_t)warp * 32 * PPL * 8;
-            // points of this warp's slice that exist (all of them except in the last tile)
-            const int nvalid = (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst));
-            float xs[PPL], ys[PPL], m[PPL];
-            bool exin[PPL];
-            if (nvalid == 32 * PPL && !((M & 1) && wfirst + 32 * PPL == M)) {
-#pragma unroll
-                for (int q = 0; q < PPL; ++q) {
-                    float x, y;
-                    if (INT) {
-                        const int2 v = ((const int2 *)stage)[32 * q + lane];
-                        x = (float)v.x;
-                        y = (float)v.y;
-                    } else {
-                        const float2 v = ((const float2 *)stage)[32 * q + lane];
-                        x = v.x;
-                        y = v.y;
-                    }
-                    exin[q] = INT ? int_exact(x, y) : true;
-                    xs[q] = x - ox;  // local coordinates x = p - o
-                    ys[q] = y - oy;
-                }
+            const bool whole = wfirst + 32 * PPL < M || (wfirst + 32 * PPL == M && !(M & 1));
+            if (whole) {
+                if (center)
+                    consume_slice<NE, PPL, INT, MIN3, true, false>(cx, stage, pts, M, wfirst, lane, mask,
+                                                                   vec_store, myqueue, &s_refined);
+                else
+                    consume_slice<NE, PPL, INT, MIN3, false, false>(cx, stage, pts, M, wfirst, lane, mask,
+                                                                    vec_store, myqueue, &s_refined);
             } else {
-                // the last tile: points past M are set to the origin and masked
-                // below; an odd last point is not in the bulk copy
-#pragma unroll
-                for (int q = 0; q < PPL; ++q) {
-                    const int r = 32 * q + lane;
-                    float x = ox, y = oy;
-                    if (r < nvalid) {
-                        const int64_t p = wfirst + r;
-                        if (p == M - 1 && (M & 1)) {
-                            if (INT) {
-                                x = (float)((const int32_t *)pts)[2 * p];
-                                y = (float)((const int32_t *)pts)[2 * p + 1];
-                            } else {
-                                x = ((const float *)pts)[2 * p];
-                                y = ((const float *)pts)[2 * p + 1];
-                            }
-                        } else if (INT) {
-                            const int2 v = ((const int2 *)stage)[r];
-                            x = (float)v.x;
-                            y = (float)v.y;
-                        } else {
-                            const float2 v = ((const float2 *)stage)[r];
-                            x = v.x;
-                            y = v.y;
-                        }
-                    }
-                    exin[q] = INT ? int_exact(x, y) : true;
-                    xs[q] = x - ox;
-                    ys[q] = y - oy;
-                }
-            }
-            // m = min_k s_k.  The min ignores a NaN operand, so a point with a
-            // non-finite coordinate is caught by its bound below instead.
-            if (NE > 0) {
-                if (MIN3 && NE >= 3) {
-#pragma unroll
-                    for (int q = 0; q < PPL; ++q) {
-                        float acc = fmaf(-xs[q], cwx[0], fmaf(-ys[q], cwy[0], ct[0]));
-#pragma unroll
-                        for (int k = 1; k + 1 < (NE > 0 ? NE : 1); k += 2) {
-                            const float s1 = fmaf(-xs[q], cwx[k], fmaf(-ys[q], cwy[k], ct[k]));
-                            const float s2 = fmaf(-xs[q], cwx[k + 1], fmaf(-ys[q], cwy[k + 1], ct[k + 1]));
-                            acc = fmin3(acc, s1, s2);
-                        }
-                        if ((NE & 1) == 0) {
-                            const int k = (NE > 0 ? NE : 1) - 1;
-                            acc = fminf(acc, fmaf(-xs[q], cwx[k], fmaf(-ys[q], cwy[k], ct[k])));
-                        }
-                        m[q] = acc;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
-#pragma unroll
-                        for (int q = 0; q < PPL; ++q) {
-                            const float sk = fmaf(-xs[q], cwx[k], fmaf(-ys[q], cwy[k], ct[k]));
-                            m[q] = k == 0 ? sk : fminf(m[q], sk);
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < PPL; ++q) m[q] = INFINITY;
-                for (int k = 0; k < npad; k += 4) {
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const float4 c = cs[k + kk];
-#pragma unroll
-                        for (int q = 0; q < PPL; ++q)
-                            m[q] = fminf(m[q], fmaf(-xs[q], c.x, fmaf(-ys[q], c.y, c.z)));
-                    }
-                }
-            }
-            // decisions: one ballot per 32 points for "inside", one vote per
-            // slice for "anything uncertain"
-            uint32_t w_in[PPL];
-            bool unc[PPL];
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < PPL; ++q) {
-                // B >= beta0 + beta1 max(|x|, |y|); |x| + |y| also turns a NaN
-                // or infinite coordinate into a B that is not finite, and such
-                // points are never decided here
-                const float B = fmaf(b1, fabsf(xs[q]) + fabsf(ys[q]), b0);
-                const bool valid = 32 * q + lane < nvalid;
-                const bool fin = B < INFINITY;
-                const bool in = (m[q] >= B) && fin && exin[q] && valid;
-                unc[q] = (!(fabsf(m[q]) >= B) || !fin || !exin[q]) && valid;
-                any |= unc[q];
-                w_in[q] = __ballot_sync(0xffffffffu, in);
-            }
-            if (__any_sync(0xffffffffu, any)) {
-                // rare: queue the uncertain points; they are decided after the
-                // tile loop, when the coefficient registers are free
-#pragma unroll
-                for (int q = 0; q < PPL; ++q) {
-                    const uint32_t u = __ballot_sync(0xffffffffu, unc[q]);
-                    if (u) {
-                        unsigned int base = 0;
-                        if (lane == 0) base = atomicAdd(&s_refined, (unsigned int)__popc(u));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (unc[q]) myqueue[base + __popc(u & ((1u << lane) - 1u))] = (uint32_t)(wfirst + 32 * q + lane);
-                    }
-                }
-            }
-            // the slice's mask words: PPL consecutive words
-            const int nw = (nvalid + 31) >> 5;
-            uint32_t *mw = mask + (wfirst >> 5);
-            if (vec_store && nw == PPL && (PPL % 4) == 0) {
-                if (lane == 0) {
-#pragma unroll
-                    for (int q = 0; q < PPL; q += 4)
-                        *(uint4 *)(mw + q) = make_uint4(w_in[q], w_in[q + 1], w_in[q + 2], w_in[q + 3]);
-                }
-            } else {
-                uint32_t myword = 0;
-#pragma unroll
-                for (int q = 0; q < PPL; ++q)
-                    if (lane == q) myword = w_in[q];
-                if (lane < nw) mw[lane] = myword;
+                consume_slice<NE, PPL, INT, MIN3, true, true>(cx, stage, pts, M, wfirst, lane, mask,
+                                                              vec_store, myqueue, &s_refined);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);

@@ -69,7 +69,7 @@ cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int
 struct StreamVariant {
     int ppl, stages, min3;
 };
-constexpr StreamVariant kStreamVariants[] = {{8, 4, 0}, {8, 4, 1}, {8, 3, 0}, {16, 2, 0}};
+constexpr StreamVariant kStreamVariants[] = {{8, 4, 0}, {8, 6, 0}, {8, 3, 0}, {16, 2, 0}};
 constexpr int kNumStreamVariants = sizeof(kStreamVariants) / sizeof(kStreamVariants[0]);
 
 template <int NE, int PPL, int STAGES, bool INT, bool MIN3>
@@ -130,7 +130,7 @@ cudaError_t launch_stream_tma(const pip_tables *t, const void *pts, int64_t M, u
                               cudaStream_t s)
 {
     switch (t->stream_variant) {
-    case 1: return launch_tma_ne<8, 4, INT, true>(t, pts, M, mask, s);
+    case 1: return launch_tma_ne<8, 6, INT, false>(t, pts, M, mask, s);
     case 2: return launch_tma_ne<8, 3, INT, false>(t, pts, M, mask, s);
     case 3: return launch_tma_ne<16, 2, INT, false>(t, pts, M, mask, s);
     default: return launch_tma_ne<8, 4, INT, false>(t, pts, M, mask, s);
@@ -144,7 +144,7 @@ namespace pip {
 cudaError_t stream_kernels_setup()
 {
     cudaError_t e = set_smem_attr<8, 4, false>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 4, true>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 6, false>();
     if (e == cudaSuccess) e = set_smem_attr<8, 3, false>();
     if (e == cudaSuccess) e = set_smem_attr<16, 2, false>();
     return e;
