@@ -81,7 +81,9 @@ typedef struct pip_tables pip_tables;
  *
  * The vertices are copied; the caller's buffers may be freed afterwards.
  * Allocates device memory (cudaMalloc), so it must not be called while a
- * stream is being captured.  Per-polygon validation runs on the device; an
+ * stream is being captured.  With one polygon it also synchronizes `stream`
+ * once, to keep a host copy of the polygon's coefficients that pip_test then
+ * passes to its kernel as launch parameters.  Per-polygon validation runs on the device; an
  * invalid polygon contains no point, and pip_get_status reports the worst
  * problem.  Returns PIP_OK, PIP_E_INVALID_ARG or PIP_E_CUDA.
  */

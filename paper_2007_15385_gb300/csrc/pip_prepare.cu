@@ -122,6 +122,17 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
                                                   t->d_coefn, t->d_poly, t->d_worst);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && num_polygons == 1) {
+        // one polygon: keep its row and coefficients on the host too, so that
+        // the pipelined kernel receives them as launch parameters
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaMemcpy(&t->h_poly, t->d_poly, sizeof(PolyInfo), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            const int n = total_vertices < kMaxEdges ? total_vertices : kMaxEdges;
+            e = cudaMemcpy(t->h_coef, t->d_coef, (size_t)n * sizeof(float4), cudaMemcpyDeviceToHost);
+        }
+        if (e == cudaSuccess) t->have_host_poly = 1;
+    }
     if (e != cudaSuccess) {
         cudaFree(t->base);
         free(t);

@@ -115,11 +115,19 @@ struct StreamCfg {
     static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
 };
 
-template <int NE>
-struct SliceCtx {
+// The polygon as launch parameters: read from the constant bank by the
+// FMAs themselves (no registers, no loads).  Edges past n carry w = 0,
+// t = +inf; an invalid polygon carries one edge with t = -inf.
+constexpr int kParamEdges = 16;
+struct StreamPoly {
     float ox, oy, b0, b1;
-    const float *cwx, *cwy, *ct;  // register-resident coefficients (NE > 0)
-    const float4 *cs;             // shared-memory coefficients (NE == 0)
+    int n, ok, pad0, pad1;
+    float wx[kParamEdges], wy[kParamEdges], t[kParamEdges];
+};
+
+struct SliceCtx {
+    const StreamPoly *sp;  // launch parameters (NE > 0)
+    const float4 *cs;      // shared-memory coefficients (NE == 0)
     int npad;
 };
 
@@ -128,18 +136,19 @@ struct SliceCtx {
 // run past M (or hold the odd last point, which is not in the bulk copy).
 // CENTER: subtract the local origin o (false when o = (0, 0)).
 template <int NE, int PPL, bool INT, bool MIN3, bool CENTER, bool TAIL>
-__device__ __forceinline__ void consume_slice(const SliceCtx<NE> &cx, const unsigned char *stage,
+__device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned char *stage,
                                               const void *__restrict__ pts, int64_t M, int64_t wfirst,
                                               int lane, uint32_t *__restrict__ mask, bool vec_store,
                                               uint32_t *__restrict__ myqueue, unsigned int *s_queued)
 {
     const int nvalid = TAIL ? (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst)) : 32 * PPL;
+    const StreamPoly &sp = *cx.sp;
     float xs[PPL], ys[PPL], m[PPL];
     bool exin[PPL];
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
         const int r = 32 * q + lane;
-        float x = cx.ox, y = cx.oy;
+        float x = sp.ox, y = sp.oy;
         if (!TAIL || r < nvalid) {
             if (TAIL && wfirst + r == M - 1 && (M & 1)) {
                 const int64_t p = M - 1;
@@ -161,8 +170,8 @@ __device__ __forceinline__ void consume_slice(const SliceCtx<NE> &cx, const unsi
             }
         }
         exin[q] = INT ? int_exact(x, y) : true;
-        xs[q] = CENTER ? x - cx.ox : x;  // local coordinates x = p - o
-        ys[q] = CENTER ? y - cx.oy : y;
+        xs[q] = CENTER ? x - sp.ox : x;  // local coordinates x = p - o
+        ys[q] = CENTER ? y - sp.oy : y;
     }
     // m = min_k s_k, NaN-propagating so that a non-finite point stays undecided
     if (NE > 0) {
@@ -170,7 +179,7 @@ __device__ __forceinline__ void consume_slice(const SliceCtx<NE> &cx, const unsi
         for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
-                const float sk = fmaf(-xs[q], cx.cwx[k], fmaf(-ys[q], cx.cwy[k], cx.ct[k]));
+                const float sk = fmaf(-xs[q], sp.wx[k], fmaf(-ys[q], sp.wy[k], sp.t[k]));
                 m[q] = k == 0 ? sk : fmin_nan(m[q], sk);
             }
         }
@@ -193,7 +202,9 @@ __device__ __forceinline__ void consume_slice(const SliceCtx<NE> &cx, const unsi
     bool any = false;
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
-        const float B = fmaf(cx.b1, fmaxf(fabsf(xs[q]), fabsf(ys[q])), cx.b0);
+        // B >= beta0 + beta1 max(|x|, |y|), formed on the FMA pipe; a NaN or
+        // infinite coordinate makes m NaN or B infinite, never "decided in"
+        const float B = fmaf(sp.b1, fabsf(xs[q]) + fabsf(ys[q]), sp.b0);
         const bool valid = !TAIL || 32 * q + lane < nvalid;
         const bool in = (m[q] >= B) && (!INT || exin[q]) && valid;
         unc[q] = (!(fabsf(m[q]) >= B) || (INT && !exin[q])) && valid;
@@ -237,7 +248,7 @@ __device__ __forceinline__ void consume_slice(const SliceCtx<NE> &cx, const unsi
 // MIN3: take the running min three operands at a time.
 template <int NE, int PPL, int STAGES, bool INT, bool MIN3>
 __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBlocks) stream_tma_kernel(
-    const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
+    const __grid_constant__ StreamPoly sp, const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
     const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab,
     const void *__restrict__ verts, int vdtype, const void *__restrict__ pts, int64_t M,
     uint32_t *__restrict__ mask, uint32_t *__restrict__ queue, StreamCounters *__restrict__ ctr,
@@ -252,17 +263,17 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
     __shared__ unsigned int s_refined;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const PolyInfo pi = poly[0];
-    const bool ok = pi.status == PIP_OK;
-    const int n = ok ? pi.n : 1;
+    const int n = sp.ok ? sp.n : 1;
     const int npad = (n + 3) & ~3;
-    // edges past n never win the min (w = 0, t = +inf); an invalid polygon is
-    // one edge with t = -inf and contains nothing
-    for (int k = tid; k < npad; k += blockDim.x) {
-        float4 c;
-        if (!ok) c = k == 0 ? make_float4(0.f, 0.f, -INFINITY, 0.f) : make_float4(0.f, 0.f, INFINITY, 0.f);
-        else c = k < n ? coef[pi.voff + k] : make_float4(0.f, 0.f, INFINITY, 0.f);
-        cs[k] = c;
+    if (NE == 0) {
+        // more edges than the parameter block holds: stage them in shared memory
+        const PolyInfo pi = poly[0];
+        for (int k = tid; k < npad; k += blockDim.x) {
+            float4 c;
+            if (!sp.ok) c = k == 0 ? make_float4(0.f, 0.f, -INFINITY, 0.f) : make_float4(0.f, 0.f, INFINITY, 0.f);
+            else c = k < n ? coef[pi.voff + k] : make_float4(0.f, 0.f, INFINITY, 0.f);
+            cs[k] = c;
+        }
     }
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -305,21 +316,10 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
         }
     } else {
         // ---------------- consumers
-        const float ox = pi.ox, oy = pi.oy, b0 = pi.beta0, b1 = pi.beta1;
         // o = (0, 0) when prepare chose the origin itself: no centring needed
-        const bool center = !(ox == 0.f && oy == 0.f);
-        float cwx[NE > 0 ? NE : 1], cwy[NE > 0 ? NE : 1], ct[NE > 0 ? NE : 1];
-        if (NE > 0) {
-#pragma unroll
-            for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
-                const float4 c = k < npad ? cs[k] : make_float4(0.f, 0.f, INFINITY, 0.f);
-                cwx[k] = c.x;
-                cwy[k] = c.y;
-                ct[k] = c.z;
-            }
-        }
+        const bool center = !(sp.ox == 0.f && sp.oy == 0.f);
         const bool vec_store = ((uintptr_t)mask & 15) == 0;
-        SliceCtx<NE> cx{ox, oy, b0, b1, cwx, cwy, ct, cs, npad};
+        SliceCtx cx{&sp, cs, npad};
         for (int64_t it = 0; it < mine; ++it) {
             const int s = (int)(it % STAGES);
             if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), err)) break;

@@ -69,7 +69,7 @@ cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int
 struct StreamVariant {
     int ppl, stages, min3;
 };
-constexpr StreamVariant kStreamVariants[] = {{8, 4, 0}, {8, 6, 0}, {8, 3, 0}, {16, 2, 0}};
+constexpr StreamVariant kStreamVariants[] = {{16, 3, 0}, {16, 2, 0}, {8, 4, 0}, {8, 6, 0}};
 constexpr int kNumStreamVariants = sizeof(kStreamVariants) / sizeof(kStreamVariants[0]);
 
 template <int NE, int PPL, int STAGES, bool INT, bool MIN3>
@@ -84,7 +84,24 @@ cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint
     if (per_sm > 2) per_sm = 2;  // the scratch queue holds one tile of slack per CTA, 2 CTAs per SM
     const int64_t tiles = (M + C::kTile - 1) / C::kTile;
     const int blocks = (int)max((int64_t)1, min((int64_t)per_sm * t->num_sms, tiles));
-    k<<<blocks, kStreamThreads, C::kSmem, s>>>(t->d_poly, t->d_coef, t->d_g0, t->d_gk, t->d_verts,
+    StreamPoly sp;
+    const PolyInfo &hp = t->h_poly;
+    sp.ox = hp.ox;
+    sp.oy = hp.oy;
+    sp.b0 = hp.beta0;
+    sp.b1 = hp.beta1;
+    sp.ok = hp.status == PIP_OK;
+    sp.n = sp.ok ? hp.n : 1;
+    sp.pad0 = sp.pad1 = 0;
+    for (int k = 0; k < kParamEdges; ++k) {
+        float4 c = make_float4(0.f, 0.f, INFINITY, 0.f);
+        if (!sp.ok) { if (k == 0) c.z = -INFINITY; }
+        else if (k < sp.n) c = t->h_coef[k];
+        sp.wx[k] = c.x;
+        sp.wy[k] = c.y;
+        sp.t[k] = c.z;
+    }
+    k<<<blocks, kStreamThreads, C::kSmem, s>>>(sp, t->d_poly, t->d_coef, t->d_g0, t->d_gk, t->d_verts,
                                                t->vdtype, pts, M, mask, t->d_queue,
                                                (StreamCounters *)t->d_stream_ctr, t->d_qcount, t->d_error);
     return cudaGetLastError();
@@ -130,10 +147,10 @@ cudaError_t launch_stream_tma(const pip_tables *t, const void *pts, int64_t M, u
                               cudaStream_t s)
 {
     switch (t->stream_variant) {
-    case 1: return launch_tma_ne<8, 6, INT, false>(t, pts, M, mask, s);
-    case 2: return launch_tma_ne<8, 3, INT, false>(t, pts, M, mask, s);
-    case 3: return launch_tma_ne<16, 2, INT, false>(t, pts, M, mask, s);
-    default: return launch_tma_ne<8, 4, INT, false>(t, pts, M, mask, s);
+    case 1: return launch_tma_ne<16, 2, INT, false>(t, pts, M, mask, s);
+    case 2: return launch_tma_ne<8, 4, INT, false>(t, pts, M, mask, s);
+    case 3: return launch_tma_ne<8, 6, INT, false>(t, pts, M, mask, s);
+    default: return launch_tma_ne<16, 3, INT, false>(t, pts, M, mask, s);
     }
 }
 
@@ -143,10 +160,10 @@ namespace pip {
 
 cudaError_t stream_kernels_setup()
 {
-    cudaError_t e = set_smem_attr<8, 4, false>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 6, false>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 3, false>();
+    cudaError_t e = set_smem_attr<16, 3, false>();
     if (e == cudaSuccess) e = set_smem_attr<16, 2, false>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 4, false>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 6, false>();
     return e;
 }
 
@@ -197,7 +214,7 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
                           : launch_ragged<true, false>(t, d_points, num_points, d_point_offsets, mask, s);
         else e = v16 ? launch_ragged<false, true>(t, d_points, num_points, d_point_offsets, mask, s)
                      : launch_ragged<false, false>(t, d_points, num_points, d_point_offsets, mask, s);
-    } else if (t->P == 1 && !want_hit && v16) {
+    } else if (t->P == 1 && !want_hit && v16 && t->have_host_poly) {
         // the pipelined kernel: bulk test and exact refine in one launch
         timing_mark(t, 0, s);
         e = ints ? launch_stream_tma<true>(t, d_points, num_points, mask, s)
