@@ -196,39 +196,32 @@ __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned
             }
         }
     }
-    // decisions: one ballot per 32 points for "inside"; "uncertain" is |m| < B,
-    // read off the sign bit of |m| - B and OR-ed over the slice, so that a
-    // single vote tells whether the slice has any.  (A NaN or infinite
-    // coordinate gives m NaN or B infinite: never "inside", and outside is the
-    // right answer for it.)
+    // decisions: one ballot per 32 points for "inside", one vote for the slice
     uint32_t w_in[PPL];
-    uint32_t signs = 0;
+    bool unc[PPL];
+    bool any = false;
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
+        // B >= beta0 + beta1 max(|x|, |y|), formed on the FMA pipe; a NaN or
+        // infinite coordinate makes m NaN or B infinite, never "decided in"
         const float B = fmaf(sp.b1, fabsf(xs[q]) + fabsf(ys[q]), sp.b0);
         const bool valid = !TAIL || 32 * q + lane < nvalid;
         const bool in = (m[q] >= B) && (!INT || exin[q]) && valid;
-        uint32_t sg = __float_as_uint(fabsf(m[q]) - B);
-        if (INT && !exin[q]) sg = 0x80000000u;
-        if (TAIL && !valid) sg = 0u;
-        signs |= sg;
+        unc[q] = (!(fabsf(m[q]) >= B) || (INT && !exin[q])) && valid;
+        any |= unc[q];
         w_in[q] = __ballot_sync(0xffffffffu, in);
     }
-    const bool any = (signs >> 31) != 0;
     if (__any_sync(0xffffffffu, any)) {
         // rare: queue the uncertain points; they are decided after the tile
         // loop, when the coefficient registers are free
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
-            const float B = fmaf(sp.b1, fabsf(xs[q]) + fabsf(ys[q]), sp.b0);
-            const bool valid = !TAIL || 32 * q + lane < nvalid;
-            const bool unc = valid && ((fabsf(m[q]) - B < 0.f) || (INT && !exin[q]));
-            const uint32_t u = __ballot_sync(0xffffffffu, unc);
+            const uint32_t u = __ballot_sync(0xffffffffu, unc[q]);
             if (u) {
                 unsigned int base = 0;
                 if (lane == 0) base = atomicAdd(s_queued, (unsigned int)__popc(u));
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (unc) myqueue[base + __popc(u & ((1u << lane) - 1u))] = (uint32_t)(wfirst + 32 * q + lane);
+                if (unc[q]) myqueue[base + __popc(u & ((1u << lane) - 1u))] = (uint32_t)(wfirst + 32 * q + lane);
             }
         }
     }
