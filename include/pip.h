@@ -228,6 +228,43 @@ pip_status pip_test_voronoi_fp64(const pip_tables *t, const float *d_points,
                                  uint32_t *d_mask, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Differentiable collision penalty (motion-planning use of the margin):
+ *
+ *   L = sum_pose sum_point softplus(-m(R(theta)^T (p - t)) / tau)
+ *
+ * with m the Voronoi margin of pip_margin (the signed distance from the Eq. 2
+ * bisectors), of one convex footprint given in its body frame.  The gradient
+ * flows through the margin's maximising edge (lowest index among ties), the
+ * mirrored generators (Eq. 8) and the centroid (Eq. 3-4) to the vertices, and
+ * through the rigid transform to the poses.  Each call rebuilds the
+ * generators from the vertices (nothing is carried from forward to
+ * backward).  Each block keeps float32 partial sums (per-edge sums of the
+ * backward pass through shared-memory atomics, whose order is not fixed);
+ * the per-block partials are fp64 and are added in a fixed order.
+ *
+ *   d_vertices   device float [num_vertices][2], 3..64 vertices, 8-byte aligned
+ *   d_poses      device float [num_poses][3] = (t_x, t_y, theta)
+ *   d_points     device float [num_points][2], 8-byte aligned
+ *   tau          > 0, in the units of the coordinates
+ *   d_workspace  device, >= pip_penalty_workspace_bytes(...) bytes, 256-byte
+ *                aligned, owned by the caller; nothing is allocated
+ *   d_loss       device double [1]
+ *   d_grad_loss  device float [1] (the upstream dL_total/dL) or NULL for 1
+ *   d_grad_vertices device double [num_vertices][2];  d_grad_poses device double [num_poses][3]
+ *
+ * An invalid footprint (see pip_prepare) gives loss 0 and zero gradients.
+ * No host synchronisation.
+ * ------------------------------------------------------------------------ */
+size_t pip_penalty_workspace_bytes(int32_t num_vertices, int32_t num_poses, int64_t num_points);
+pip_status pip_penalty_forward(const float *d_vertices, int32_t num_vertices, const float *d_poses,
+                               int32_t num_poses, const float *d_points, int64_t num_points, float tau,
+                               double *d_loss, void *d_workspace, size_t workspace_bytes, void *stream);
+pip_status pip_penalty_backward(const float *d_vertices, int32_t num_vertices, const float *d_poses,
+                                int32_t num_poses, const float *d_points, int64_t num_points, float tau,
+                                const float *d_grad_loss, double *d_grad_vertices, double *d_grad_poses,
+                                void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * pip_test_single_noalloc -- the paper has no counterpart to this call; it
  * exists for callers that cannot allocate device memory when they test
  * points: a fixed-rate control loop (a vehicle's collision check) that cannot

@@ -53,6 +53,11 @@ SIGNATURES = {
     "pip_test_voronoi_fp64": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "pip_test_single_noalloc": (_INT, [_P, _INT, _I32, _P, _INT, _I64, _P, _P, _P]),
     "pip_stream_variant_count": (_I32, []),
+    "pip_penalty_workspace_bytes": (ctypes.c_size_t, [_I32, _I32, _I64]),
+    "pip_penalty_forward": (_INT, [_P, _I32, _P, _I32, _P, _I64, ctypes.c_float, _P, _P,
+                                    ctypes.c_size_t, _P]),
+    "pip_penalty_backward": (_INT, [_P, _I32, _P, _I32, _P, _I64, ctypes.c_float, _P, _P, _P, _P,
+                                     ctypes.c_size_t, _P]),
     "pip_set_stream_variant": (_INT, [_P, _I32]),
     "pip_autotune_stream": (_INT, [_P, _P, _INT, _I64, _P, _I32, _P, ctypes.POINTER(_I32),
                                     ctypes.POINTER(ctypes.c_float)]),
@@ -330,3 +335,71 @@ def pip_test_single_noalloc(vertices: torch.Tensor, points: torch.Tensor, mask: 
                                          status.data_ptr() if status is not None else None,
                                          _stream(stream)), "pip_test_single_noalloc")
     return mask
+
+
+def pip_penalty_workspace_bytes(num_vertices: int, num_poses: int, num_points: int) -> int:
+    return int(lib().pip_penalty_workspace_bytes(num_vertices, num_poses, num_points))
+
+
+def _penalty_ws(vertices, poses, points):
+    nb = pip_penalty_workspace_bytes(vertices.numel() // 2, poses.numel() // 3, points.numel() // 2)
+    return torch.empty(nb, dtype=torch.uint8, device=vertices.device)
+
+
+def pip_penalty_forward(vertices: torch.Tensor, poses: torch.Tensor, points: torch.Tensor, tau: float,
+                        workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Collision penalty sum softplus(-margin/tau) over poses x points; fp64 scalar tensor."""
+    for t_, nm in ((vertices, "vertices"), (poses, "poses"), (points, "points")):
+        _dev(t_, nm)
+        if t_.dtype != torch.float32:
+            raise TypeError("%s must be float32" % nm)
+    ws = workspace if workspace is not None else _penalty_ws(vertices, poses, points)
+    loss = torch.empty(1, dtype=torch.float64, device=vertices.device)
+    _check(lib().pip_penalty_forward(vertices.data_ptr(), vertices.numel() // 2, poses.data_ptr(),
+                                     poses.numel() // 3, points.data_ptr(), points.numel() // 2,
+                                     float(tau), loss.data_ptr(), ws.data_ptr(), ws.numel(),
+                                     _stream(stream)), "pip_penalty_forward")
+    return loss[0]
+
+
+def pip_penalty_backward(vertices: torch.Tensor, poses: torch.Tensor, points: torch.Tensor, tau: float,
+                         grad_loss: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                         stream=None):
+    """(d loss/d vertices [n, 2] fp64, d loss/d poses [P, 3] fp64), scaled by grad_loss."""
+    ws = workspace if workspace is not None else _penalty_ws(vertices, poses, points)
+    gv = torch.empty((vertices.numel() // 2, 2), dtype=torch.float64, device=vertices.device)
+    gp = torch.empty((poses.numel() // 3, 3), dtype=torch.float64, device=vertices.device)
+    go = None
+    if grad_loss is not None:
+        go = grad_loss.detach().to(device=vertices.device, dtype=torch.float32).reshape(1).contiguous()
+    _check(lib().pip_penalty_backward(vertices.data_ptr(), vertices.numel() // 2, poses.data_ptr(),
+                                      poses.numel() // 3, points.data_ptr(), points.numel() // 2,
+                                      float(tau), go.data_ptr() if go is not None else None,
+                                      gv.data_ptr(), gp.data_ptr(), ws.data_ptr(), ws.numel(),
+                                      _stream(stream)), "pip_penalty_backward")
+    return gv, gp
+
+
+class CollisionPenalty(torch.autograd.Function):
+    """L = sum_pose sum_point softplus(-margin(R^T (p - t)) / tau) with hand-written CUDA
+    forward and backward kernels; gradients for the footprint vertices and the poses (the
+    obstacle points are data).  The generator tables are rebuilt in backward."""
+
+    @staticmethod
+    def forward(ctx, vertices, poses, points, tau: float):
+        v = vertices.detach().contiguous()
+        p = poses.detach().contiguous()
+        q = points.detach().contiguous()
+        ctx.save_for_backward(v, p, q)
+        ctx.tau = float(tau)
+        return pip_penalty_forward(v, p, q, ctx.tau)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        v, p, q = ctx.saved_tensors
+        gv, gp = pip_penalty_backward(v, p, q, ctx.tau, grad_loss=grad_out)
+        return gv.to(v.dtype), gp.to(p.dtype), None, None
+
+
+def collision_penalty(vertices, poses, points, tau: float):
+    return CollisionPenalty.apply(vertices, poses, points, tau)

@@ -1,0 +1,126 @@
+"""GPU parity of the collision penalty (forward, hand-written backward, autograd).
+
+The oracle's fp64 loss and analytic gradient (pinned in test_oracle_pins.py by
+central differences and by the closed-form point-to-line gradient) are the
+reference.  Gradients must agree to 1e-4 relative, both norm-wise and
+elementwise (against max(|g_ref|, 1e-3 |g_ref|_inf)).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2007_15385_gb300 import binding as B
+from paper_2007_15385_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.lib()
+    yield
+
+
+def _to(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _rel_ok(got, want, tol=1e-4):
+    got = np.asarray(got, float).ravel()
+    want = np.asarray(want, float).ravel()
+    nrm = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300)
+    floor = 1e-3 * np.abs(want).max()
+    elem = np.abs(got - want) <= tol * np.maximum(np.abs(want), floor)
+    return nrm <= tol and elem.all(), nrm, int((~elem).sum())
+
+
+def _case(m=8192, poses=12, seed=40):
+    w = wl.footprint_trajectory(seed=seed, m=m, num_poses=poses)
+    return w.vertices, w.extra["poses"], w.points, w.extra["tau"]
+
+
+def test_penalty_loss_and_gradients_match_fp64_reference():
+    v, P, q, tau = _case()
+    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau).item()
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    ref_loss, ref_gv, ref_gp = oracle.penalty(v.astype(np.float64), P.astype(np.float64),
+                                             q.astype(np.float64), tau)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
+    assert ok, "vertex gradient: norm-wise %.2e, %d elements off" % (nrm, bad)
+    ok, nrm, bad = _rel_ok(gp.cpu().numpy(), ref_gp)
+    assert ok, "pose gradient: norm-wise %.2e, %d elements off" % (nrm, bad)
+
+
+def test_penalty_gradient_against_central_differences_of_fp64_loss():
+    v, P, q, tau = _case(m=2048, poses=4, seed=41)
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    gv = gv.cpu().numpy()
+    gp = gp.cpu().numpy()
+    vd, Pd, qd = v.astype(np.float64), P.astype(np.float64), q.astype(np.float64)
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    for _ in range(8):
+        i, d = int(rng.integers(len(v))), int(rng.integers(2))
+        vp, vm = vd.copy(), vd.copy()
+        vp[i, d] += h
+        vm[i, d] -= h
+        fd = (oracle.penalty_loss(vp, Pd, qd, tau) - oracle.penalty_loss(vm, Pd, qd, tau)) / (2 * h)
+        assert gv[i, d] == pytest.approx(fd, rel=1e-4, abs=1e-4 * np.abs(gv).max())
+    for j in range(len(P)):
+        for d in range(3):
+            pp, pm = Pd.copy(), Pd.copy()
+            pp[j, d] += h
+            pm[j, d] -= h
+            fd = (oracle.penalty_loss(vd, pp, qd, tau) - oracle.penalty_loss(vd, pm, qd, tau)) / (2 * h)
+            assert gp[j, d] == pytest.approx(fd, rel=1e-4, abs=1e-4 * np.abs(gp).max())
+
+
+def test_penalty_autograd_function():
+    v, P, q, tau = _case(m=4096, poses=6, seed=42)
+    vt = _to(v).requires_grad_(True)
+    pt = _to(P).requires_grad_(True)
+    loss = B.collision_penalty(vt, pt, _to(q), tau)
+    (3.0 * loss).backward()
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    np.testing.assert_allclose(vt.grad.cpu().numpy(), 3.0 * gv.cpu().numpy(), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(pt.grad.cpu().numpy(), 3.0 * gp.cpu().numpy(), rtol=1e-6, atol=1e-6)
+
+
+def test_penalty_translation_invariance_on_gpu():
+    v, P, q, tau = _case(m=4096, poses=5, seed=43)
+    l0 = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau).item()
+    shift = np.array([4.0, -2.0], np.float32)
+    P2 = P.copy()
+    P2[:, :2] += shift
+    l1 = B.pip_penalty_forward(_to(v), _to(P2), _to(q + shift), tau).item()
+    assert l1 == pytest.approx(l0, rel=1e-5)
+
+
+def test_penalty_empty_points_and_invalid_footprint():
+    v, P, q, tau = _case(m=16, poses=2, seed=44)
+    assert B.pip_penalty_forward(_to(v), _to(P), _to(q[:0]), tau).item() == 0.0
+    bad = np.array([[0, 0], [2, 0], [1, 0.2], [2, 2], [0, 2]], np.float32)  # non-convex
+    assert B.pip_penalty_forward(_to(bad), _to(P), _to(q), tau).item() == 0.0
+    gv, gp = B.pip_penalty_backward(_to(bad), _to(P), _to(q), tau)
+    assert not gv.cpu().numpy().any() and not gp.cpu().numpy().any()
+
+
+def test_penalty_full_size_sampled_poses():
+    """The full workload (256 poses x 2^20 points, the benchmark's launch
+    shape); poses are independent, so each sampled pose's gradient must match
+    the oracle on that pose alone."""
+    w = wl.footprint_trajectory()
+    v, P, q, tau = w.vertices, w.extra["poses"], w.points, w.extra["tau"]
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    gp = gp.cpu().numpy()
+    rng = np.random.default_rng(5)
+    for j in rng.choice(len(P), size=3, replace=False):
+        _, _, ref_gp = oracle.penalty(v.astype(np.float64), P[j:j + 1].astype(np.float64),
+                                      q.astype(np.float64), tau)
+        ok, nrm, bad = _rel_ok(gp[j], ref_gp[0])
+        assert ok, "pose %d: norm-wise %.2e" % (j, nrm)
+    assert np.isfinite(gv.cpu().numpy()).all()
