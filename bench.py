@@ -184,6 +184,10 @@ def main():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--points", type=int, default=NUM_POINTS,
                     help="points of the workload (default the full 2^26; smaller only for profiling)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "gis_batch", "gis_all_pairs", "integer_hulls",
+                             "footprint_trajectory", "unit_circle_octagon"],
+                    help="which workload to time (the default is the headline)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="tile shape of the pipelined kernel (default: autotuned)")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
@@ -193,6 +197,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != WORKLOAD:
+        return run_other(args)
 
     import torch
     import torch.distributed as dist
@@ -348,6 +354,111 @@ def main():
     t.close()
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def fp32_fma_peak_tflops(sm_mhz: float) -> tuple[float, int]:
+    """#SM x 128 FP32 lanes x 2 flop x clock (clock sampled during the run)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms
+
+
+def time_steps(fn, steps: int, warmup: int, stream) -> float:
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_other(args):
+    """One JSON line for a workload other than the headline (same metric and unit)."""
+    import torch
+
+    from paper_2007_15385_gb300 import binding as B
+    from paper_2007_15385_gb300 import workloads as wl
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    gen = {"gis_batch": wl.gis_batch, "gis_all_pairs": wl.gis_all_pairs,
+           "integer_hulls": wl.integer_hulls, "footprint_trajectory": wl.footprint_trajectory,
+           "unit_circle_octagon": wl.unit_circle_octagon}[args.workload]
+    w = gen()
+    v = torch.from_numpy(w.vertices).to(dev)
+    vo = torch.from_numpy(w.vertex_offsets).to(dev)
+    p = torch.from_numpy(w.points).to(dev)
+    po = torch.from_numpy(w.point_offsets).to(dev) if w.point_offsets is not None else None
+    M = w.num_points
+    tests = w.tests()
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    extra = {}
+    if args.workload == "footprint_trajectory":
+        poses = torch.from_numpy(w.extra["poses"]).to(dev)
+        tau = w.extra["tau"]
+        ws = torch.empty(B.pip_penalty_workspace_bytes(len(w.vertices), len(poses), M),
+                         dtype=torch.uint8, device=dev)
+        n = len(w.vertices)
+        tests = len(poses) * M * n
+        fwd = time_steps(lambda: B.pip_penalty_forward(v, poses, p, tau, workspace=ws),
+                         args.steps, args.warmup, stream)
+        bwd = time_steps(lambda: B.pip_penalty_backward(v, poses, p, tau, workspace=ws),
+                         args.steps, args.warmup, stream)
+        ms = fwd
+        extra = {"forward_ms": fwd, "backward_ms": bwd,
+                 "forward_Gtests_per_s": tests / (fwd * 1e-3) / 1e9,
+                 "backward_Gtests_per_s": tests / (bwd * 1e-3) / 1e9,
+                 "pairs": len(poses) * M}
+        launches = 4
+    else:
+        t = B.pip_prepare(v, vo, max_points=M)
+        mode = B.PIP_MASK | (B.PIP_FIRST_HIT if args.workload == "gis_all_pairs" else 0)
+        mask = torch.empty((M + 31) // 32, dtype=torch.int32, device=dev)
+        hit = torch.empty(M, dtype=torch.int32, device=dev) if mode & B.PIP_FIRST_HIT else None
+        call = lambda: B.pip_test(t, p, po, mode=mode, mask=mask, first_hit=hit)
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize()
+        B.pip_timing(t, True)
+        ms = time_steps(call, args.steps, 0, stream)
+        calls, bulk_ms, refine_ms = B.pip_timing_read(t)
+        _, refined = B.pip_get_status(t)
+        extra = {"bulk_kernel_ms": bulk_ms / max(1, calls), "refine_kernel_ms": refine_ms / max(1, calls),
+                 "refined_points_per_step": refined, "refine_fraction": refined / max(1, M)}
+        launches = 3 if po is not None else (1 if (len(w.vertex_offsets) == 2 and p.data_ptr() % 16 == 0) else 2)
+        t.close()
+    clk = clocks.stop()
+    value = tests / (ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "num_points": M, "num_polygons": w.num_polygons,
+                       "tests_per_step": tests},
+            "clocks": clk, "gpu_launches": launches * args.steps}
+    line.update(extra)
+    if args.workload in ("gis_all_pairs", "footprint_trajectory", "gis_batch", "integer_hulls"):
+        tflops, sms = fp32_fma_peak_tflops(clk["sm_mhz"] or 2070.0)
+        kernel_ms = extra.get("bulk_kernel_ms", ms)
+        achieved = 2.0 * tests / (kernel_ms * 1e-3) / 1e12
+        line["fma_roofline"] = {"bound": "alu", "achieved": achieved, "peak": tflops, "unit": "TFLOP/s",
+                                "frac": achieved / tflops,
+                                "peak_kind": "%d SMs x 128 FP32 lanes x 2 x sampled SM clock" % sms}
+    if args.workload in ("gis_batch", "integer_hulls"):
+        peak, kind = measured_peaks()
+        kernel_ms = extra["bulk_kernel_ms"]
+        achieved = (M * 8 + ((M + 31) // 32) * 4) / (kernel_ms * 1e-3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "peak_kind": kind + " hbm_gbs"}
+    print(json.dumps(line))
     return 0
 
 
