@@ -446,12 +446,13 @@ def run_other(args):
             "clocks": clk, "gpu_launches": launches * args.steps}
     line.update(extra)
     if args.workload in ("gis_all_pairs", "footprint_trajectory", "gis_batch", "integer_hulls"):
+        # every test is two FMAs (4 flops): s_k = t_k - x w_kx - y w_ky
         tflops, sms = fp32_fma_peak_tflops(clk["sm_mhz"] or 2070.0)
         kernel_ms = extra.get("bulk_kernel_ms", ms)
-        achieved = 2.0 * tests / (kernel_ms * 1e-3) / 1e12
+        achieved = 4.0 * tests / (kernel_ms * 1e-3) / 1e12
         line["fma_roofline"] = {"bound": "alu", "achieved": achieved, "peak": tflops, "unit": "TFLOP/s",
                                 "frac": achieved / tflops,
-                                "peak_kind": "%d SMs x 128 FP32 lanes x 2 x sampled SM clock" % sms}
+                                "peak_kind": "%d SMs x 128 FP32 FMA lanes x 2 flop x sampled SM clock" % sms}
     if args.workload in ("gis_batch", "integer_hulls"):
         peak, kind = measured_peaks()
         kernel_ms = extra["bulk_kernel_ms"]
