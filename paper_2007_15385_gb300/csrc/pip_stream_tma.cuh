@@ -173,14 +173,20 @@ __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned
         xs[q] = CENTER ? x - sp.ox : x;  // local coordinates x = p - o
         ys[q] = CENTER ? y - sp.oy : y;
     }
-    // m = min_k s_k, NaN-propagating so that a non-finite point stays undecided
+    // m = min_k s_k, NaN-propagating so that a non-finite point stays undecided;
+    // three operands per min (NE is a multiple of 4)
     if (NE > 0) {
 #pragma unroll
-        for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
+        for (int q = 0; q < PPL; ++q)
+            m[q] = fmin_nan(fmaf(-xs[q], sp.wx[0], fmaf(-ys[q], sp.wy[0], sp.t[0])),
+                            fmaf(-xs[q], sp.wx[1], fmaf(-ys[q], sp.wy[1], sp.t[1])));
+#pragma unroll
+        for (int k = 2; k < (NE > 0 ? NE : 2); k += 2) {
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
-                const float sk = fmaf(-xs[q], sp.wx[k], fmaf(-ys[q], sp.wy[k], sp.t[k]));
-                m[q] = k == 0 ? sk : fmin_nan(m[q], sk);
+                const float s1 = fmaf(-xs[q], sp.wx[k], fmaf(-ys[q], sp.wy[k], sp.t[k]));
+                const float s2 = fmaf(-xs[q], sp.wx[k + 1], fmaf(-ys[q], sp.wy[k + 1], sp.t[k + 1]));
+                m[q] = fmin3_nan(m[q], s1, s2);
             }
         }
     } else {
@@ -294,11 +300,13 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
     if (warp == kConsumerWarps) {
         // ---------------- producer: one elected lane issues the bulk copies
         if (lane == 0) {
-            int64_t it = 0;
-            for (; it < mine; ++it) {
-                const int s = (int)(it % STAGES);
-                if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)((it / STAGES - 1) & 1), err)) break;
-                const int64_t first = ((int64_t)blockIdx.x + it * gridDim.x) * kTile;
+            const int nmine = (int)mine;
+            int it = 0, s = 0;
+            uint32_t ephase = 0;  // parity of the empty-barrier phase to wait for
+            int64_t first = (int64_t)blockIdx.x * kTile;
+            const int64_t step = (int64_t)gridDim.x * kTile;
+            for (; it < nmine; ++it) {
+                if (it >= STAGES && !mbar_wait(&empty[s], ephase, err)) break;
                 const int64_t cnt = min((int64_t)kTile, M - first);
                 const uint32_t bytes = (uint32_t)(cnt * 8) & ~15u;  // an odd last point is read directly
                 if (bytes) {
@@ -307,10 +315,15 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                 } else {
                     mbar_arrive(&full[s]);
                 }
+                first += step;
+                if (++s == STAGES) {
+                    s = 0;
+                    if (it + 1 >= 2 * STAGES) ephase ^= 1u;  // round r >= 1 waits for parity (r - 1) & 1
+                }
             }
-            if (it < mine) {
+            if (it < nmine) {
                 // gave up: let the copies already issued land before the CTA leaves
-                for (int64_t k = it > STAGES ? it - STAGES : 0; k < it; ++k)
+                for (int k = it > STAGES ? it - STAGES : 0; k < it; ++k)
                     mbar_wait(&full[k % STAGES], (uint32_t)((k / STAGES) & 1), err);
             }
         }
@@ -320,13 +333,17 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
         const bool center = !(sp.ox == 0.f && sp.oy == 0.f);
         const bool vec_store = ((uintptr_t)mask & 15) == 0;
         SliceCtx cx{&sp, cs, npad};
-        for (int64_t it = 0; it < mine; ++it) {
-            const int s = (int)(it % STAGES);
-            if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), err)) break;
-            const int64_t first = ((int64_t)blockIdx.x + it * gridDim.x) * kTile;
-            const int64_t wfirst = first + warp * 32 * PPL;
+        const int nmine = (int)mine;
+        int s = 0;
+        uint32_t fphase = 0;
+        int64_t wfirst = (int64_t)blockIdx.x * kTile + warp * 32 * PPL;
+        const int64_t step = (int64_t)gridDim.x * kTile;
+        // slices that end before the last point (or at an even end) need no bounds logic
+        const int64_t whole_end = (M & 1) ? M - 1 : M;
+        for (int it = 0; it < nmine; ++it, wfirst += step) {
+            if (!mbar_wait(&full[s], fphase, err)) break;
             const unsigned char *stage = smem + (size_t)s * C::kStageBytes + (size_t)warp * 32 * PPL * 8;
-            const bool whole = wfirst + 32 * PPL < M || (wfirst + 32 * PPL == M && !(M & 1));
+            const bool whole = wfirst + 32 * PPL <= whole_end;
             if (whole) {
                 if (center)
                     consume_slice<NE, PPL, INT, MIN3, true, false>(cx, stage, pts, M, wfirst, lane, mask,
@@ -340,6 +357,10 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
+            if (++s == STAGES) {
+                s = 0;
+                fphase ^= 1u;
+            }
         }
     }
     __syncthreads();

@@ -60,13 +60,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    for (;;) {
+        // the clock is read once per 64 tries, so that waiting costs few issue slots
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
         if (clock64() - t0 > kWaitCycles) {
             atomicExch(err, (int)PIP_E_TIMEOUT);
             return false;
         }
     }
-    return true;
 }
 
 // bytes (multiple of 16) from 16-byte aligned global src to 16-byte aligned
