@@ -37,13 +37,16 @@ WORKLOAD = "vehicle_footprint"
 NUM_POINTS = 1 << 26
 FALLBACK_HBM_GBS = 6800.0
 
-# dram bytes (read + write) per launch of the streaming kernel on this
-# workload, from one ncu capture (profiles/stream_kernel_vehicle_footprint.md),
+# dram bytes (read + write) per launch of the pipelined kernel on this
+# workload, from one ncu capture (profiles/stream_tma_kernel_vehicle_footprint.md)
+# of 2^25 points scaled by 2 to the 2^26-point launch,
 # valid only while the kernel sources hash to the value recorded with it.
-NCU_TRAFFIC = {"bytes": 549259264, "sources_sha": "a0aef079207fae9c"}
-KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_test_kernels.cuh",
+NCU_TRAFFIC = {"bytes": 549280768, "sources_sha": "16bd9b79266c8de2"}
+KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_stream_tma.cuh",
+                  "paper_2007_15385_gb300/csrc/pip_tma.cuh",
                   "paper_2007_15385_gb300/csrc/pip_kernels.cuh",
-                  "paper_2007_15385_gb300/csrc/pip_internal.cuh"]
+                  "paper_2007_15385_gb300/csrc/pip_internal.cuh",
+                  "paper_2007_15385_gb300/csrc/pip_test.cu"]
 
 
 def sources_sha() -> str:
