@@ -89,6 +89,7 @@ struct pip_tables {
     float4 *d_coefn;
     pip::PolyInfo *d_poly;
     uint32_t *d_queue;
+    uint32_t *d_keys;            // [max_points] all-pairs candidate keys
     int64_t *d_items;            // [P+1] work-item prefix of the own-polygon schedule
     unsigned int *d_qcount;      // refine queue length of the last pip_test
     unsigned int *d_work;        // next work item of the persistent kernel

@@ -86,6 +86,8 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     // per-CTA slices (at most one tile of 4,096 points per CTA, 2 CTAs per SM)
     const size_t queue_entries = (size_t)max_points + (size_t)(2 * t->num_sms + 1) * 4096;
     const size_t o_queue = take(queue_entries * sizeof(uint32_t));
+    // all-pairs candidate keys (also used by one polygon when a first hit is asked for)
+    const size_t o_keys = take((size_t)(max_points > 0 ? max_points : 1) * sizeof(uint32_t));
     t->bytes = off;
     if (cudaMalloc(&t->base, t->bytes) != cudaSuccess) {
         free(t);
@@ -106,6 +108,7 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     t->d_error = (int32_t *)(b + o_cnt + 48);
     t->d_stream_ctr = (void *)(b + o_cnt + 64);
     t->d_queue = (uint32_t *)(b + o_queue);
+    t->d_keys = (uint32_t *)(b + o_keys);
 
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;

@@ -28,76 +28,6 @@ struct StreamCounters {
     unsigned int ticket;
 };
 
-__device__ __forceinline__ void point_d(const void *pts, int dtype, int64_t i, double &x, double &y)
-{
-    if (dtype == PIP_I32) {
-        const int32_t *q = (const int32_t *)pts;
-        x = (double)q[2 * i];
-        y = (double)q[2 * i + 1];
-    } else {
-        const float *f = (const float *)pts;
-        x = (double)f[2 * i];
-        y = (double)f[2 * i + 1];
-    }
-}
-
-// Exact inclusion of point i in polygon j, decided by the whole warp (every
-// lane calls it with the same arguments; lane l takes edges l and l + 32).
-// Integer inputs: int64 cross products.  Otherwise: the fp64 Voronoi
-// comparison from the stored generators, and the exact orientation sign
-// where that comparison is within its bound.
-__device__ __noinline__ bool warp_inside_exact(const PolyInfo *__restrict__ poly, int j,
-                                               const double2 *__restrict__ g0tab,
-                                               const double2 *__restrict__ gk,
-                                               const void *__restrict__ verts, int vdtype,
-                                               const void *__restrict__ pts, int pdtype, int64_t i)
-{
-    const int lane = threadIdx.x & 31;
-    const PolyInfo pi = poly[j];
-    if (pi.status != PIP_OK) return false;
-    const int n = pi.n, v0 = pi.voff, sigma = pi.orient;
-    bool out = false;
-    if (vdtype == PIP_I32 && pdtype == PIP_I32) {
-        const int32_t *q = (const int32_t *)pts;
-        const int64_t px = q[2 * i], py = q[2 * i + 1];
-        const int32_t *v = (const int32_t *)verts;
-        for (int k = lane; k < n; k += 32) {
-            const int km = k == 0 ? n - 1 : k - 1;
-            const int64_t ax = v[2 * (v0 + km)], ay = v[2 * (v0 + km) + 1];
-            const int64_t bx = v[2 * (v0 + k)], by = v[2 * (v0 + k) + 1];
-            // |b - a| <= 2^25 and |p - a| < 2^32 + 2^24: each product < 2^58
-            const int64_t cr = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
-            if ((cr > 0 ? 1 : (cr < 0 ? -1 : 0)) == -sigma) out = true;
-        }
-        return !__any_sync(0xffffffffu, out);
-    }
-    double px, py;
-    point_d(pts, pdtype, i, px, py);
-    if (!isfinite(px) || !isfinite(py)) return false;
-    const double2 g0 = g0tab[j];
-    const double e = pi.gerr;
-    const double ap = fmax(fabs(px), fabs(py));
-    for (int k = lane; k < n; k += 32) {
-        const double2 g = gk[v0 + k];
-        const double dx = g.x - g0.x, dy = g.y - g0.y;                        // p_k - p0
-        const double sx = g.x + g0.x - 2.0 * px, sy = g.y + g0.y - 2.0 * py;  // p_k + p0 - 2x
-        const double d = dx * sx + dy * sy;  // |x - p_k|^2 - |x - p0|^2
-        const double mag = fmax(fmax(fabs(g.x), fabs(g.y)), fmax(fmax(fabs(g0.x), fabs(g0.y)), ap));
-        const double bound = 8.0 * e * (fabs(sx) + fabs(sy) + fabs(dx) + fabs(dy) + 4.0 * e) +
-                             ldexp((fabs(dx) + fabs(dy)) * (fabs(sx) + fabs(sy) + 4.0 * mag), -48);
-        if (d < -bound) {
-            out = true;
-        } else if (!(d > bound)) {
-            const int km = k == 0 ? n - 1 : k - 1;
-            double ax, ay, bx, by;
-            point_d(verts, vdtype, v0 + km, ax, ay);
-            point_d(verts, vdtype, v0 + k, bx, by);
-            if (orient_sign_exact(ax, ay, bx, by, px, py) == -sigma) out = true;
-        }
-    }
-    return !__any_sync(0xffffffffu, out);
-}
-
 constexpr int kConsumerWarps = 8;
 constexpr int kStreamThreads = (kConsumerWarps + 1) * 32;
 

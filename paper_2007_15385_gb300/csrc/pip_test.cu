@@ -54,14 +54,190 @@ cudaError_t launch_ragged(const pip_tables *t, const void *pts, int64_t M, const
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// All pairs, split over point tiles and polygon ranges.  Each thread keeps
+// AP_PT points in registers and evaluates every polygon of its block's range
+// (full work: no early exit, no cull); the polygons stream through shared
+// memory in chunks.  Per point the lowest "candidate" polygon -- decided
+// inside, or uncertain -- is kept as the key (j << 1) | uncertain and merged
+// over the ranges with atomicMin; a finalize pass turns keys into first-hit
+// ids and mask words and queues the points whose lowest candidate is
+// uncertain.
+// ---------------------------------------------------------------------------
+constexpr int kApPT = 8;
+constexpr int kApThreads = 256;
+constexpr int kApChunk = 32;  // polygons per shared-memory chunk
+constexpr int kApSplit = 4;   // polygon ranges per point tile
+
+template <bool INT>
+__global__ void __launch_bounds__(kApThreads) allpairs_split_kernel(
+    const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef, int P, const void *__restrict__ pts,
+    int64_t M, uint32_t *__restrict__ keys)
+{
+    __shared__ float4 cs[kApChunk * (kMaxEdges + 4)];
+    __shared__ float4 so[kApChunk];  // (ox, oy, beta0, beta1)
+    __shared__ int sn[kApChunk];     // padded edge count
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t base = (int64_t)blockIdx.x * (kApPT * kApThreads);
+    const int per = (P + gridDim.y - 1) / gridDim.y;
+    const int jlo = blockIdx.y * per, jhi = min(P, jlo + per);
+    float px[kApPT], py[kApPT];
+    bool exin[kApPT];
+    uint32_t key[kApPT];
+#pragma unroll
+    for (int i = 0; i < kApPT; ++i) {
+        const int64_t p = base + i * kApThreads + tid;
+        px[i] = p < M ? load_coord(pts, INT ? PIP_I32 : PIP_F32, 2 * p) : 0.f;
+        py[i] = p < M ? load_coord(pts, INT ? PIP_I32 : PIP_F32, 2 * p + 1) : 0.f;
+        exin[i] = INT ? int_exact(px[i], py[i]) : true;
+        key[i] = 0xffffffffu;
+    }
+    for (int j0 = jlo; j0 < jhi; j0 += kApChunk) {
+        const int nj = min(kApChunk, jhi - j0);
+        __syncthreads();
+        if (tid < nj) {
+            const PolyInfo pi = poly[j0 + tid];
+            so[tid] = make_float4(pi.ox, pi.oy, pi.beta0, pi.beta1);
+            sn[tid] = ((pi.status == PIP_OK ? pi.n : 1) + 3) & ~3;
+        }
+        for (int q = tid >> 5; q < nj; q += kApThreads / 32)
+            stage_polygon(poly[j0 + q], coef, cs + q * (kMaxEdges + 4), lane, 32);
+        __syncthreads();
+        for (int q = 0; q < nj; ++q) {
+            const float4 o = so[q];
+            const int npad = sn[q];
+            const float4 *c = cs + q * (kMaxEdges + 4);
+            float x[kApPT], y[kApPT], m[kApPT];
+#pragma unroll
+            for (int i = 0; i < kApPT; ++i) {
+                x[i] = px[i] - o.x;
+                y[i] = py[i] - o.y;
+                m[i] = INFINITY;
+            }
+            for (int k = 0; k < npad; k += 4) {
+                const float4 c0 = c[k], c1 = c[k + 1], c2 = c[k + 2], c3 = c[k + 3];
+#pragma unroll
+                for (int i = 0; i < kApPT; ++i) {
+                    const float s0 = fmaf(-x[i], c0.x, fmaf(-y[i], c0.y, c0.z));
+                    const float s1 = fmaf(-x[i], c1.x, fmaf(-y[i], c1.y, c1.z));
+                    const float s2 = fmaf(-x[i], c2.x, fmaf(-y[i], c2.y, c2.z));
+                    const float s3 = fmaf(-x[i], c3.x, fmaf(-y[i], c3.y, c3.z));
+                    m[i] = fmin3_nan(fmin3_nan(m[i], s0, s1), s2, s3);
+                }
+            }
+            const uint32_t jj = (uint32_t)(j0 + q) << 1;
+#pragma unroll
+            for (int i = 0; i < kApPT; ++i) {
+                const float B = fmaf(o.w, fabsf(x[i]) + fabsf(y[i]), o.z);
+                const bool in = (m[i] >= B) && exin[i];
+                const bool unc = !(fabsf(m[i]) >= B) || !exin[i];
+                if (key[i] == 0xffffffffu && (in || unc)) key[i] = jj | (in ? 0u : 1u);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kApPT; ++i) {
+        const int64_t p = base + i * kApThreads + tid;
+        if (p < M && key[i] != 0xffffffffu) atomicMin(&keys[p], key[i]);
+    }
+}
+
+// keys -> first-hit ids, mask words, refine queue
+__global__ void __launch_bounds__(kThreads) allpairs_finalize_kernel(
+    const uint32_t *__restrict__ keys, int64_t M, int32_t *__restrict__ first_hit, uint32_t *__restrict__ mask,
+    uint32_t *__restrict__ queue, unsigned int *__restrict__ qcount)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t end = (M + 31) & ~(int64_t)31;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end; p += stride) {
+        const uint32_t k = p < M ? keys[p] : 0xffffffffu;
+        const bool decided_in = k != 0xffffffffu && !(k & 1u);
+        const bool unc = k != 0xffffffffu && (k & 1u);
+        if (p < M && first_hit) first_hit[p] = decided_in ? (int32_t)(k >> 1) : -1;
+        const uint32_t w = __ballot_sync(0xffffffffu, decided_in);
+        if (mask && lane == 0) mask[p >> 5] = w;
+        const uint32_t u = __ballot_sync(0xffffffffu, unc);
+        if (u) {
+            unsigned int qb = 0;
+            if (lane == 0) qb = atomicAdd(qcount, (unsigned int)__popc(u));
+            qb = __shfl_sync(0xffffffffu, qb, 0);
+            if (unc) queue[qb + __popc(u & ((1u << lane) - 1u))] = (uint32_t)p;
+        }
+    }
+}
+
 template <bool INT>
 cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int32_t *first_hit,
                             uint32_t *mask, cudaStream_t s)
 {
-    const int64_t blocks = (M + kPT * kThreads - 1) / (kPT * kThreads);
-    allpairs_kernel<kPT, INT><<<(unsigned)blocks, kThreads, 0, s>>>(
-        t->d_poly, t->d_coef, t->P, pts, M, first_hit, mask, t->d_queue, t->d_qcount);
+    cudaError_t e = cudaMemsetAsync(t->d_keys, 0xff, (size_t)M * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (M + kApPT * kApThreads - 1) / (kApPT * kApThreads);
+    const int split = t->P < kApSplit ? t->P : kApSplit;
+    allpairs_split_kernel<INT><<<dim3((unsigned)tiles, (unsigned)split), kApThreads, 0, s>>>(
+        t->d_poly, t->d_coef, t->P, pts, M, t->d_keys);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    allpairs_finalize_kernel<<<t->num_sms * 4, kThreads, 0, s>>>(t->d_keys, M, first_hit, mask, t->d_queue,
+                                                                 t->d_qcount);
     return cudaGetLastError();
+}
+
+// Warp-cooperative refine for float inputs and for the all-pairs test: one
+// warp per queued point.  Own-polygon or single mode: the lanes split the
+// polygon's edges (warp_inside_exact).  All pairs: the lanes take 32
+// polygons at a time and make the float32 decision of each; the lowest
+// polygon that is decided inside, or is uncertain and then found inside
+// exactly, is the first hit.
+__global__ void __launch_bounds__(kThreads) refine_warp_kernel(RefineArgs A, int mode)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned int count = *A.qcount;
+    const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < count; q += nwarps) {
+        const int64_t i = A.queue[q];
+        if (mode == kAllPairs) {
+            // the lowest candidate is uncertain: scan upward from it
+            const int start = (int)(A.keys[i] >> 1);
+            const int limit = A.P;
+            int hit = -1;
+            for (int base = start; base < limit; base += 32) {
+                const int j = base + lane;
+                const int b = j < limit ? bulk_decision(A, j, i) : -1;
+                const uint32_t in_m = __ballot_sync(0xffffffffu, b > 0);
+                uint32_t cand = in_m | __ballot_sync(0xffffffffu, b == 0);
+                bool found = false;
+                while (cand) {
+                    const int l = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    if (((in_m >> l) & 1u) ||
+                        warp_inside_exact(A.poly, base + l, A.g0, A.gk, A.verts, A.vdtype, A.pts, A.pdtype, i)) {
+                        hit = base + l;
+                        found = true;
+                        break;
+                    }
+                }
+                if (found) break;
+            }
+            if (lane == 0) {
+                if (A.first_hit) A.first_hit[i] = hit;
+                if (A.mask && hit >= 0) atomicOr(&A.mask[i >> 5], 1u << (i & 31));
+            }
+        } else {
+            int j = 0;
+            if (mode == kRagged) {
+                int lo = 0, hi = A.P;  // poffs[lo] <= i < poffs[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (A.poffs[mid] <= i) lo = mid; else hi = mid;
+                }
+                j = lo;
+            }
+            if (warp_inside_exact(A.poly, j, A.g0, A.gk, A.verts, A.vdtype, A.pts, A.pdtype, i) && lane == 0)
+                atomicOr(&A.mask[i >> 5], 1u << (i & 31));
+        }
+    }
 }
 
 // Variants of the pipelined kernel: (points per lane per stage, stages,
@@ -259,7 +435,11 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     A.qcount = t->d_qcount;
     A.mask = mask;
     A.first_hit = hit;
-    refine_kernel<<<t->num_sms * 2, kThreads, 0, s>>>(A, kmode);
+    A.keys = t->d_keys;
+    if (kmode != kAllPairs && t->vdtype == PIP_I32 && pdtype == PIP_I32)
+        refine_kernel<<<t->num_sms * 2, kThreads, 0, s>>>(A, kmode);  // int64, one thread a point
+    else
+        refine_warp_kernel<<<t->num_sms * 4, kThreads, 0, s>>>(A, kmode);
     if (cudaGetLastError() != cudaSuccess) return PIP_E_CUDA;
     timing_mark(t, 2, s);
     return PIP_OK;

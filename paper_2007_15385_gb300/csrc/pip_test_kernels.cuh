@@ -289,6 +289,7 @@ struct RefineArgs {
     const unsigned int *qcount;
     uint32_t *mask;
     int32_t *first_hit;
+    const uint32_t *keys;  // all-pairs candidate keys (pip_test's split path)
 };
 
 __device__ __forceinline__ void vertex_d(const void *verts, int vdtype, int64_t i, double &x, double &y)
