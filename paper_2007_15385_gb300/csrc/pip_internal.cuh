@@ -21,6 +21,8 @@ namespace pip {
 
 constexpr int kMaxEdges = 64;
 constexpr int kMinEdges = 3;
+// Row stride of the padded coefficient table: 64 edges rounded up, plus room.
+constexpr int kPadStride = kMaxEdges + 4;
 // Integer vertices must satisfy |v| <= 2^24 so that float32 holds them exactly
 // and every exact cross product fits in int64.
 constexpr int32_t kIntLimit = 1 << 24;
@@ -87,6 +89,7 @@ struct pip_tables {
     double2 *d_gk;
     float4 *d_coef;
     float4 *d_coefn;
+    float4 *d_coefp;             // [P][kPadStride] coefficients padded per polygon (all pairs)
     pip::PolyInfo *d_poly;
     uint32_t *d_queue;
     uint32_t *d_keys;            // [max_points] all-pairs candidate keys
@@ -134,6 +137,7 @@ bool aligned(const void *p, size_t a);
 // Implemented in pip_test.cu: raises the dynamic shared-memory limit of the
 // pipelined kernels on the current device (outside any stream capture).
 cudaError_t stream_kernels_setup();
+cudaError_t allpairs_setup();
 int stream_variant_count();
 }  // namespace pip
 

@@ -26,6 +26,27 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// One warp per polygon: its coefficients at row j of a fixed-stride table,
+// padded to a multiple of 4 edges with edges that never win the min
+// (w = 0, t = +inf); an invalid polygon is one edge with t = -inf.
+__global__ void pad_coef_kernel(const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef, int P,
+                                float4 *__restrict__ coefp)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    if (j >= P) return;
+    const PolyInfo pi = poly[j];
+    const bool ok = pi.status == PIP_OK;
+    const int n = ok ? pi.n : 1;
+    const int npad = (n + 3) & ~3;
+    for (int k = lane; k < npad; k += 32) {
+        float4 c;
+        if (!ok) c = k == 0 ? make_float4(0.f, 0.f, -INFINITY, 0.f) : make_float4(0.f, 0.f, INFINITY, 0.f);
+        else c = k < n ? coef[pi.voff + k] : make_float4(0.f, 0.f, INFINITY, 0.f);
+        coefp[(size_t)j * kPadStride + k] = c;
+    }
+}
+
 }  // namespace
 
 namespace pip {
@@ -79,6 +100,7 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     const size_t o_gk = take(V * sizeof(double2));
     const size_t o_coef = take(V * sizeof(float4));
     const size_t o_coefn = take(V * sizeof(float4));
+    const size_t o_coefp = take(num_polygons > 1 ? P * kPadStride * sizeof(float4) : 16);
     const size_t o_poly = take(P * sizeof(PolyInfo));
     const size_t o_items = take((P + 1) * sizeof(int64_t));
     const size_t o_cnt = take(128);
@@ -100,6 +122,7 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     t->d_gk = (double2 *)(b + o_gk);
     t->d_coef = (float4 *)(b + o_coef);
     t->d_coefn = (float4 *)(b + o_coefn);
+    t->d_coefp = (float4 *)(b + o_coefp);
     t->d_poly = (PolyInfo *)(b + o_poly);
     t->d_items = (int64_t *)(b + o_items);
     t->d_qcount = (unsigned int *)(b + o_cnt);
@@ -117,12 +140,19 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
         e = cudaMemcpyAsync(t->d_voffs, d_vertex_offsets, (P + 1) * 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt, 0, 128, s);
     if (e == cudaSuccess) e = stream_kernels_setup();
+    if (e == cudaSuccess) e = allpairs_setup();
     if (e == cudaSuccess) {
         const int threads = 256;
         const int blocks = (int)((P * 32 + threads - 1) / threads);
         prepare_kernel<<<blocks, threads, 0, s>>>(t->d_verts, vdtype, t->d_voffs, num_polygons,
                                                   total_vertices, t->d_g0, t->d_gk, t->d_coef,
                                                   t->d_coefn, t->d_poly, t->d_worst);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && num_polygons > 1) {
+        const int threads = 256;
+        const int blocks = (int)((P * 32 + threads - 1) / threads);
+        pad_coef_kernel<<<blocks, threads, 0, s>>>(t->d_poly, t->d_coef, num_polygons, t->d_coefp);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && num_polygons == 1) {

@@ -69,18 +69,46 @@ constexpr int kApThreads = 256;
 constexpr int kApChunk = 32;  // polygons per shared-memory chunk
 constexpr int kApSplit = 4;   // polygon ranges per point tile
 
+// Shared memory of the all-pairs kernel: two chunk buffers, each the padded
+// coefficient rows and the PolyInfo rows of kApChunk polygons.
+constexpr size_t kApRowsBytes = (size_t)kApChunk * kPadStride * sizeof(float4);
+constexpr size_t kApInfoBytes = (size_t)kApChunk * sizeof(PolyInfo);
+constexpr size_t kApBufBytes = kApRowsBytes + kApInfoBytes;
+constexpr size_t kApSmem = 2 * kApBufBytes;
+
 template <bool INT>
-__global__ void __launch_bounds__(kApThreads) allpairs_split_kernel(
-    const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef, int P, const void *__restrict__ pts,
-    int64_t M, uint32_t *__restrict__ keys)
+__global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
+    const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, int P, const void *__restrict__ pts,
+    int64_t M, uint32_t *__restrict__ keys, int *__restrict__ err)
 {
-    __shared__ float4 cs[kApChunk * (kMaxEdges + 4)];
-    __shared__ float4 so[kApChunk];  // (ox, oy, beta0, beta1)
-    __shared__ int sn[kApChunk];     // padded edge count
-    const int tid = threadIdx.x, lane = tid & 31;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t full[2];
+    const int tid = threadIdx.x;
     const int64_t base = (int64_t)blockIdx.x * (kApPT * kApThreads);
     const int per = (P + gridDim.y - 1) / gridDim.y;
     const int jlo = blockIdx.y * per, jhi = min(P, jlo + per);
+    const int nchunks = jhi > jlo ? (jhi - jlo + kApChunk - 1) / kApChunk : 0;
+    // one elected thread streams chunks of polygons into the two buffers
+    auto issue = [&](int c) {
+        const int j0 = jlo + c * kApChunk;
+        const int nj = min(kApChunk, jhi - j0);
+        unsigned char *buf = smem + (size_t)(c & 1) * kApBufBytes;
+        const uint32_t rows = (uint32_t)(nj * kPadStride * sizeof(float4));
+        const uint32_t info = (uint32_t)(nj * sizeof(PolyInfo));
+        mbar_arrive_expect_tx(&full[c & 1], rows + info);
+        bulk_copy_g2s(buf, coefp + (size_t)j0 * kPadStride, rows, &full[c & 1]);
+        bulk_copy_g2s(buf + kApRowsBytes, poly + j0, info, &full[c & 1]);
+    };
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (nchunks > 0) issue(0);
+        if (nchunks > 1) issue(1);
+    }
     float px[kApPT], py[kApPT];
     bool exin[kApPT];
     uint32_t key[kApPT];
@@ -92,30 +120,28 @@ __global__ void __launch_bounds__(kApThreads) allpairs_split_kernel(
         exin[i] = INT ? int_exact(px[i], py[i]) : true;
         key[i] = 0xffffffffu;
     }
-    for (int j0 = jlo; j0 < jhi; j0 += kApChunk) {
+    int c = 0;
+    for (; c < nchunks; ++c) {
+        if (!mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), err)) break;
+        const unsigned char *buf = smem + (size_t)(c & 1) * kApBufBytes;
+        const float4 *rows = (const float4 *)buf;
+        const PolyInfo *info = (const PolyInfo *)(buf + kApRowsBytes);
+        const int j0 = jlo + c * kApChunk;
         const int nj = min(kApChunk, jhi - j0);
-        __syncthreads();
-        if (tid < nj) {
-            const PolyInfo pi = poly[j0 + tid];
-            so[tid] = make_float4(pi.ox, pi.oy, pi.beta0, pi.beta1);
-            sn[tid] = ((pi.status == PIP_OK ? pi.n : 1) + 3) & ~3;
-        }
-        for (int q = tid >> 5; q < nj; q += kApThreads / 32)
-            stage_polygon(poly[j0 + q], coef, cs + q * (kMaxEdges + 4), lane, 32);
-        __syncthreads();
         for (int q = 0; q < nj; ++q) {
-            const float4 o = so[q];
-            const int npad = sn[q];
-            const float4 *c = cs + q * (kMaxEdges + 4);
+            const PolyInfo &pi = info[q];
+            const float ox = pi.ox, oy = pi.oy, b0 = pi.beta0, b1 = pi.beta1;
+            const int npad = ((pi.status == PIP_OK ? pi.n : 1) + 3) & ~3;
+            const float4 *cf = rows + q * kPadStride;
             float x[kApPT], y[kApPT], m[kApPT];
 #pragma unroll
             for (int i = 0; i < kApPT; ++i) {
-                x[i] = px[i] - o.x;
-                y[i] = py[i] - o.y;
+                x[i] = px[i] - ox;
+                y[i] = py[i] - oy;
                 m[i] = INFINITY;
             }
             for (int k = 0; k < npad; k += 4) {
-                const float4 c0 = c[k], c1 = c[k + 1], c2 = c[k + 2], c3 = c[k + 3];
+                const float4 c0 = cf[k], c1 = cf[k + 1], c2 = cf[k + 2], c3 = cf[k + 3];
 #pragma unroll
                 for (int i = 0; i < kApPT; ++i) {
                     const float s0 = fmaf(-x[i], c0.x, fmaf(-y[i], c0.y, c0.z));
@@ -128,12 +154,18 @@ __global__ void __launch_bounds__(kApThreads) allpairs_split_kernel(
             const uint32_t jj = (uint32_t)(j0 + q) << 1;
 #pragma unroll
             for (int i = 0; i < kApPT; ++i) {
-                const float B = fmaf(o.w, fabsf(x[i]) + fabsf(y[i]), o.z);
+                const float B = fmaf(b1, fabsf(x[i]) + fabsf(y[i]), b0);
                 const bool in = (m[i] >= B) && exin[i];
                 const bool unc = !(fabsf(m[i]) >= B) || !exin[i];
                 if (key[i] == 0xffffffffu && (in || unc)) key[i] = jj | (in ? 0u : 1u);
             }
         }
+        __syncthreads();  // every warp is done with this buffer
+        if (tid == 0 && c + 2 < nchunks) issue(c + 2);
+    }
+    if (c < nchunks && tid == 0) {
+        // gave up waiting: let the copies still in flight land before leaving
+        for (int k = c; k < nchunks && k < c + 2; ++k) mbar_wait(&full[k & 1], (uint32_t)((k >> 1) & 1), err);
     }
 #pragma unroll
     for (int i = 0; i < kApPT; ++i) {
@@ -175,8 +207,8 @@ cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int
     if (e != cudaSuccess) return e;
     const int64_t tiles = (M + kApPT * kApThreads - 1) / (kApPT * kApThreads);
     const int split = t->P < kApSplit ? t->P : kApSplit;
-    allpairs_split_kernel<INT><<<dim3((unsigned)tiles, (unsigned)split), kApThreads, 0, s>>>(
-        t->d_poly, t->d_coef, t->P, pts, M, t->d_keys);
+    allpairs_split_kernel<INT><<<dim3((unsigned)tiles, (unsigned)split), kApThreads, kApSmem, s>>>(
+        t->d_poly, t->d_coefp, t->P, pts, M, t->d_keys, t->d_error);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     allpairs_finalize_kernel<<<t->num_sms * 4, kThreads, 0, s>>>(t->d_keys, M, first_hit, mask, t->d_queue,
@@ -344,6 +376,16 @@ cudaError_t stream_kernels_setup()
 }
 
 int stream_variant_count() { return kNumStreamVariants; }
+
+cudaError_t allpairs_setup()
+{
+    cudaError_t e = cudaFuncSetAttribute(allpairs_split_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(allpairs_split_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kApSmem);
+    return e;
+}
 
 }  // namespace pip
 
