@@ -64,7 +64,7 @@ cudaError_t launch_ragged(const pip_tables *t, const void *pts, int64_t M, const
 // ids and mask words and queues the points whose lowest candidate is
 // uncertain.
 // ---------------------------------------------------------------------------
-constexpr int kApPT = 8;
+constexpr int kApPT = 12;
 constexpr int kApThreads = 256;
 constexpr int kApChunk = 32;  // polygons per shared-memory chunk
 constexpr int kApSplit = 4;   // polygon ranges per point tile
@@ -75,6 +75,12 @@ constexpr size_t kApRowsBytes = (size_t)kApChunk * kPadStride * sizeof(float4);
 constexpr size_t kApInfoBytes = (size_t)kApChunk * sizeof(PolyInfo);
 constexpr size_t kApBufBytes = kApRowsBytes + kApInfoBytes;
 constexpr size_t kApSmem = 2 * kApBufBytes;
+
+// s_k(x) = t_k - x . w_k for one coefficient row (w_x, w_y, t_k, -), two roundings
+__device__ __forceinline__ float ap_s(const float4 &c, float x, float y)
+{
+    return fmaf(-x, c.x, fmaf(-y, c.y, c.z));
+}
 
 template <bool INT>
 __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
@@ -110,15 +116,15 @@ __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
         if (nchunks > 1) issue(1);
     }
     float px[kApPT], py[kApPT];
-    bool exin[kApPT];
     uint32_t key[kApPT];
 #pragma unroll
     for (int i = 0; i < kApPT; ++i) {
         const int64_t p = base + i * kApThreads + tid;
         px[i] = p < M ? load_coord(pts, INT ? PIP_I32 : PIP_F32, 2 * p) : 0.f;
         py[i] = p < M ? load_coord(pts, INT ? PIP_I32 : PIP_F32, 2 * p + 1) : 0.f;
-        exin[i] = INT ? int_exact(px[i], py[i]) : true;
-        key[i] = 0xffffffffu;
+        // an integer point that float32 cannot hold exactly is uncertain
+        // against the first polygon of the range, which settles its key
+        key[i] = (!INT || int_exact(px[i], py[i]) || jlo >= jhi) ? 0xffffffffu : ((uint32_t)jlo << 1) | 1u;
     }
     int c = 0;
     for (; c < nchunks; ++c) {
@@ -130,34 +136,60 @@ __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
         const int nj = min(kApChunk, jhi - j0);
         for (int q = 0; q < nj; ++q) {
             const PolyInfo &pi = info[q];
-            const float ox = pi.ox, oy = pi.oy, b0 = pi.beta0, b1 = pi.beta1;
-            const int npad = ((pi.status == PIP_OK ? pi.n : 1) + 3) & ~3;
+            if (pi.status != PIP_OK) continue;  // an invalid polygon contains no point
+            const float ox = pi.ox, oy = pi.oy;
+            const int n = pi.n;  // at least 3
             const float4 *cf = rows + q * kPadStride;
             float x[kApPT], y[kApPT], m[kApPT];
-#pragma unroll
-            for (int i = 0; i < kApPT; ++i) {
-                x[i] = px[i] - ox;
-                y[i] = py[i] - oy;
-                m[i] = INFINITY;
-            }
-            for (int k = 0; k < npad; k += 4) {
-                const float4 c0 = cf[k], c1 = cf[k + 1], c2 = cf[k + 2], c3 = cf[k + 3];
+            {
+                const float4 c0 = cf[0], c1 = cf[1], c2 = cf[2];
 #pragma unroll
                 for (int i = 0; i < kApPT; ++i) {
-                    const float s0 = fmaf(-x[i], c0.x, fmaf(-y[i], c0.y, c0.z));
-                    const float s1 = fmaf(-x[i], c1.x, fmaf(-y[i], c1.y, c1.z));
-                    const float s2 = fmaf(-x[i], c2.x, fmaf(-y[i], c2.y, c2.z));
-                    const float s3 = fmaf(-x[i], c3.x, fmaf(-y[i], c3.y, c3.z));
-                    m[i] = fmin3_nan(fmin3_nan(m[i], s0, s1), s2, s3);
+                    x[i] = px[i] - ox;
+                    y[i] = py[i] - oy;
+                    m[i] = fmin3_nan(ap_s(c0, x[i], y[i]), ap_s(c1, x[i], y[i]), ap_s(c2, x[i], y[i]));
                 }
             }
-            const uint32_t jj = (uint32_t)(j0 + q) << 1;
+            int k = 3;
+            for (; k + 4 <= n; k += 4) {
+                const float4 c0 = cf[k], c1 = cf[k + 1], c2 = cf[k + 2], c3 = cf[k + 3];
 #pragma unroll
-            for (int i = 0; i < kApPT; ++i) {
-                const float B = fmaf(b1, fabsf(x[i]) + fabsf(y[i]), b0);
-                const bool in = (m[i] >= B) && exin[i];
-                const bool unc = !(fabsf(m[i]) >= B) || !exin[i];
-                if (key[i] == 0xffffffffu && (in || unc)) key[i] = jj | (in ? 0u : 1u);
+                for (int i = 0; i < kApPT; ++i)
+                    m[i] = fmin3_nan(fmin3_nan(m[i], ap_s(c0, x[i], y[i]), ap_s(c1, x[i], y[i])),
+                                     ap_s(c2, x[i], y[i]), ap_s(c3, x[i], y[i]));
+            }
+            const int rem = n - k;  // the last 0..3 edges
+            if (rem == 1) {
+                const float4 c0 = cf[k];
+#pragma unroll
+                for (int i = 0; i < kApPT; ++i) m[i] = fmin_nan(m[i], ap_s(c0, x[i], y[i]));
+            } else if (rem == 2) {
+                const float4 c0 = cf[k], c1 = cf[k + 1];
+#pragma unroll
+                for (int i = 0; i < kApPT; ++i)
+                    m[i] = fmin3_nan(m[i], ap_s(c0, x[i], y[i]), ap_s(c1, x[i], y[i]));
+            } else if (rem == 3) {
+                const float4 c0 = cf[k], c1 = cf[k + 1], c2 = cf[k + 2];
+#pragma unroll
+                for (int i = 0; i < kApPT; ++i)
+                    m[i] = fmin3_nan(fmin_nan(m[i], ap_s(c0, x[i], y[i])), ap_s(c1, x[i], y[i]),
+                                     ap_s(c2, x[i], y[i]));
+            }
+            // Most pairs are clearly outside (m <= -B); the key update runs
+            // only when some lane of the warp holds a candidate.
+            const float b0 = pi.beta0, b1 = pi.beta1;
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < kApPT; ++i) any |= !(m[i] <= -fmaf(b1, fabsf(x[i]) + fabsf(y[i]), b0));
+            if (__any_sync(0xffffffffu, any)) {
+                const uint32_t jj = (uint32_t)(j0 + q) << 1;
+#pragma unroll
+                for (int i = 0; i < kApPT; ++i) {
+                    const float B = fmaf(b1, fabsf(x[i]) + fabsf(y[i]), b0);
+                    const bool in = m[i] >= B;
+                    const bool unc = !(fabsf(m[i]) >= B);
+                    if (key[i] == 0xffffffffu && (in || unc)) key[i] = jj | (in ? 0u : 1u);
+                }
             }
         }
         __syncthreads();  // every warp is done with this buffer
