@@ -191,6 +191,9 @@ def main():
                     choices=[WORKLOAD, "gis_batch", "gis_all_pairs", "integer_hulls",
                              "footprint_trajectory", "unit_circle_octagon"],
                     help="which workload to time (the default is the headline)")
+    ap.add_argument("--polygons", type=int, default=0,
+                    help="number of polygons of the batch workloads (0: the workload's own; "
+                         "smaller cases are for profiling)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="tile shape of the pipelined kernel (default: autotuned)")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
@@ -395,7 +398,8 @@ def run_other(args):
     gen = {"gis_batch": wl.gis_batch, "gis_all_pairs": wl.gis_all_pairs,
            "integer_hulls": wl.integer_hulls, "footprint_trajectory": wl.footprint_trajectory,
            "unit_circle_octagon": wl.unit_circle_octagon}[args.workload]
-    w = gen()
+    w = gen(num_polygons=args.polygons) if args.polygons > 0 and args.workload in (
+        "gis_batch", "gis_all_pairs", "integer_hulls") else gen()
     v = torch.from_numpy(w.vertices).to(dev)
     vo = torch.from_numpy(w.vertex_offsets).to(dev)
     p = torch.from_numpy(w.points).to(dev)

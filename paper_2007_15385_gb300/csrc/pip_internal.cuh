@@ -89,11 +89,13 @@ struct pip_tables {
     double2 *d_gk;
     float4 *d_coef;
     float4 *d_coefn;
-    float4 *d_coefp;             // [P][kPadStride] coefficients padded per polygon (all pairs)
+    float4 *d_coefp;             // [P][kPadStride] coefficients padded per polygon (all pairs, batch)
     pip::PolyInfo *d_poly;
     uint32_t *d_queue;
     uint32_t *d_keys;            // [max_points] all-pairs candidate keys
     int64_t *d_items;            // [P+1] work-item prefix of the own-polygon schedule
+    void *d_ritems;              // [ritems_cap] work items of the pipelined own-polygon kernel
+    int64_t ritems_cap;
     unsigned int *d_qcount;      // refine queue length of the last pip_test
     unsigned int *d_work;        // next work item of the persistent kernel
     int32_t *d_worst;            // worst polygon status
@@ -137,6 +139,7 @@ bool aligned(const void *p, size_t a);
 // Implemented in pip_test.cu: raises the dynamic shared-memory limit of the
 // pipelined kernels on the current device (outside any stream capture).
 cudaError_t stream_kernels_setup();
+cudaError_t ragged_kernels_setup();
 cudaError_t allpairs_setup();
 int stream_variant_count();
 }  // namespace pip

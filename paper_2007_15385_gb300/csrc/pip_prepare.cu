@@ -100,9 +100,13 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     const size_t o_gk = take(V * sizeof(double2));
     const size_t o_coef = take(V * sizeof(float4));
     const size_t o_coefn = take(V * sizeof(float4));
-    const size_t o_coefp = take(num_polygons > 1 ? P * kPadStride * sizeof(float4) : 16);
+    const size_t o_coefp = take(P * kPadStride * sizeof(float4));
     const size_t o_poly = take(P * sizeof(PolyInfo));
     const size_t o_items = take((P + 1) * sizeof(int64_t));
+    // items of the pipelined own-polygon kernel: a range [a, b) touches at most
+    // (b - a) / tile + 2 chunks of the grid (tile >= 2048 points, 16 B an item)
+    t->ritems_cap = (max_points > 0 ? max_points : 0) / 2048 + 2 * (int64_t)P + 2;
+    const size_t o_ritems = take((size_t)t->ritems_cap * 16);
     const size_t o_cnt = take(128);
     // refine queue: every point once, plus the slack of the pipelined kernel's
     // per-CTA slices (at most one tile of 4,096 points per CTA, 2 CTAs per SM)
@@ -125,6 +129,7 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     t->d_coefp = (float4 *)(b + o_coefp);
     t->d_poly = (PolyInfo *)(b + o_poly);
     t->d_items = (int64_t *)(b + o_items);
+    t->d_ritems = (void *)(b + o_ritems);
     t->d_qcount = (unsigned int *)(b + o_cnt);
     t->d_work = (unsigned int *)(b + o_cnt + 16);
     t->d_worst = (int32_t *)(b + o_cnt + 32);
@@ -141,6 +146,7 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt, 0, 128, s);
     if (e == cudaSuccess) e = stream_kernels_setup();
     if (e == cudaSuccess) e = allpairs_setup();
+    if (e == cudaSuccess) e = ragged_kernels_setup();
     if (e == cudaSuccess) {
         const int threads = 256;
         const int blocks = (int)((P * 32 + threads - 1) / threads);
@@ -149,7 +155,7 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
                                                   t->d_coefn, t->d_poly, t->d_worst);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && num_polygons > 1) {
+    if (e == cudaSuccess) {
         const int threads = 256;
         const int blocks = (int)((P * 32 + threads - 1) / threads);
         pad_coef_kernel<<<blocks, threads, 0, s>>>(t->d_poly, t->d_coef, num_polygons, t->d_coefp);

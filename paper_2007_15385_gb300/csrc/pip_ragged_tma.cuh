@@ -1,0 +1,410 @@
+// pip_ragged_tma.cuh -- the pipelined own-polygon batch: many polygons, each
+// with its own contiguous range of points (Alg. 5 per point against its own
+// polygon only).
+//
+// Schedule.  The point array is cut at a fixed grid of kTile-point chunks;
+// a work item is one polygon's points inside one chunk, {j, k, lo, hi}, the
+// points k*kTile + [lo, hi).  A single-block setup kernel validates the point
+// offsets, writes the item table (items of one polygon are consecutive) and
+// zeroes the mask words that straddle two polygons' ranges.
+//
+// Persistent CTAs, one producer warp and eight consumer warps.  The producer
+// takes the next item from a global counter (dynamic balance: polygons have
+// 3 to 64 edges and 10^3 to 10^5 points) and bulk-copies into a ring stage:
+// the item's points, the polygon's padded coefficient row and its PolyInfo
+// row; a small header names the item.  Consumers split the item into
+// 32*PPL-point slices on the chunk grid (rotating over warps from item to
+// item) and evaluate s_k = t_k - x w_kx - y w_ky with the first three edges
+// peeled, four edges per step and an exact 0-3 edge tail.  Mask words inside
+// a polygon's range are stored, words shared with a neighbour are OR-ed into
+// the zeroed word.  Uncertain points go to the global refine queue, decided
+// by the refine launch that follows.
+#pragma once
+
+#include "pip_kernels.cuh"
+#include "pip_tma.cuh"
+
+namespace {
+
+using namespace pip;
+
+struct RaggedItem {
+    int32_t j, k, lo, hi;
+};
+
+struct RaggedHeader {
+    int32_t j, k, lo, hi;
+    int32_t rot, pad0, pad1, pad2;
+};
+
+constexpr int kRaggedWarps = 8;
+constexpr int kRaggedThreads = (kRaggedWarps + 1) * 32;
+
+template <int PPL, int STAGES>
+struct RaggedCfg {
+    static constexpr int kSlice = 32 * PPL;
+    static constexpr int kTile = kRaggedWarps * kSlice;  // points per item, at most
+    static constexpr size_t kPtsBytes = (size_t)kTile * 8;
+    static constexpr size_t kCoefOff = kPtsBytes;
+    static constexpr size_t kInfoOff = kCoefOff + (size_t)kPadStride * sizeof(float4);
+    static constexpr size_t kHdrOff = kInfoOff + sizeof(PolyInfo);
+    static constexpr size_t kStageBytes = (kHdrOff + sizeof(RaggedHeader) + 127) & ~(size_t)127;
+    static constexpr size_t kBarOff = STAGES * kStageBytes;
+    static constexpr size_t kSmem = kBarOff + 2 * STAGES * sizeof(uint64_t);
+    static constexpr int kFit = (int)((227 * 1024) / (kSmem + 1024));
+    static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
+};
+
+// Single block.  Items of polygon j are the chunks of the kTile grid its
+// range [poffs[j], poffs[j+1]) touches.  Bad offsets (not a non-decreasing
+// cover of [0, M)) leave zero items and raise PIP_E_INVALID_ARG in *worst.
+__global__ void __launch_bounds__(1024) ragged_items_kernel(
+    const int64_t *__restrict__ poffs, int P, int64_t M, int tile, int64_t *__restrict__ prefix,
+    RaggedItem *__restrict__ items, int64_t cap, unsigned int *__restrict__ counters,
+    unsigned int *__restrict__ qcount, int32_t *__restrict__ worst, uint32_t *__restrict__ mask)
+{
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry;
+    __shared__ int bad;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        bad = 0;
+        counters[0] = 0;  // next item
+        *qcount = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < P; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        int64_t cnt = 0;
+        if (j < P) {
+            const int64_t a = poffs[j], b = poffs[j + 1];
+            if (a < 0 || b < a || b > M || (j == 0 && a != 0) || (j == P - 1 && b != M)) bad = 1;
+            else if (b > a) cnt = (b - 1) / tile - a / tile + 1;
+        }
+        int64_t v = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) warp_tot[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            warp_tot[lane] = w;
+        }
+        __syncthreads();
+        const int64_t excl = carry + (wid ? warp_tot[wid - 1] : 0) + v - cnt;
+        if (j < P) prefix[j] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + cnt;
+        __syncthreads();
+    }
+    const bool ok = !bad && carry <= cap;
+    if (threadIdx.x == 0) {
+        prefix[P] = ok ? carry : 0;
+        if (!ok) atomicMax(worst, (int)PIP_E_INVALID_ARG);
+    }
+    if (!ok) return;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        const int64_t a = poffs[j], b = poffs[j + 1];
+        if (b <= a) continue;
+        if (a & 31) mask[a >> 5] = 0u;
+        if (b & 31) mask[(b - 1) >> 5] = 0u;
+        int64_t i = prefix[j];
+        for (int64_t k = a / tile; k * tile < b; ++k, ++i) {
+            const int64_t c0 = k * tile;
+            RaggedItem it;
+            it.j = j;
+            it.k = (int32_t)k;
+            it.lo = (int32_t)(max(a, c0) - c0);
+            it.hi = (int32_t)(min(b, c0 + tile) - c0);
+            items[i] = it;
+        }
+    }
+}
+
+// One consumer warp, one slice: points gs + [0, 32*PPL) of which [a, b) are
+// this polygon's (TAIL: the slice is not wholly inside; the odd last point of
+// the range is not in the bulk copy and is read from global memory).
+template <int PPL, bool INT, bool CENTER, bool TAIL>
+__device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, float oy, float b0, float b1,
+                                             const unsigned char *rows, const void *__restrict__ pts,
+                                             int64_t gs, int64_t a, int64_t b, int lane,
+                                             uint32_t *__restrict__ mask, bool vec_store,
+                                             uint32_t *__restrict__ queue, unsigned int *__restrict__ qcount)
+{
+    float xs[PPL], ys[PPL], m[PPL];
+    bool exin[PPL], valid[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        const int r = 32 * q + lane;
+        const int64_t p = gs + r;
+        float x = ox, y = oy;
+        valid[q] = !TAIL || (p >= a && p < b);
+        if (valid[q]) {
+            if (TAIL && p == b - 1 && (b & 1)) {
+                if (INT) {
+                    x = (float)((const int32_t *)pts)[2 * p];
+                    y = (float)((const int32_t *)pts)[2 * p + 1];
+                } else {
+                    x = ((const float *)pts)[2 * p];
+                    y = ((const float *)pts)[2 * p + 1];
+                }
+            } else if (INT) {
+                const int2 v = ((const int2 *)rows)[r];
+                x = (float)v.x;
+                y = (float)v.y;
+            } else {
+                const float2 v = ((const float2 *)rows)[r];
+                x = v.x;
+                y = v.y;
+            }
+        }
+        exin[q] = INT ? int_exact(x, y) : true;
+        xs[q] = CENTER ? x - ox : x;
+        ys[q] = CENTER ? y - oy : y;
+    }
+    // m = min_k s_k (NaN-propagating): three edges, then four at a time, then the rest
+    {
+        const float4 c0 = cs[0], c1 = cs[1], c2 = cs[2];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            m[q] = fmin3_nan(fmaf(-xs[q], c0.x, fmaf(-ys[q], c0.y, c0.z)),
+                             fmaf(-xs[q], c1.x, fmaf(-ys[q], c1.y, c1.z)),
+                             fmaf(-xs[q], c2.x, fmaf(-ys[q], c2.y, c2.z)));
+    }
+    int k = 3;
+    for (; k + 4 <= n; k += 4) {
+        const float4 c0 = cs[k], c1 = cs[k + 1], c2 = cs[k + 2], c3 = cs[k + 3];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            const float s0 = fmaf(-xs[q], c0.x, fmaf(-ys[q], c0.y, c0.z));
+            const float s1 = fmaf(-xs[q], c1.x, fmaf(-ys[q], c1.y, c1.z));
+            const float s2 = fmaf(-xs[q], c2.x, fmaf(-ys[q], c2.y, c2.z));
+            const float s3 = fmaf(-xs[q], c3.x, fmaf(-ys[q], c3.y, c3.z));
+            m[q] = fmin3_nan(fmin3_nan(m[q], s0, s1), s2, s3);
+        }
+    }
+    const int rem = n - k;
+    if (rem == 1) {
+        const float4 c0 = cs[k];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) m[q] = fmin_nan(m[q], fmaf(-xs[q], c0.x, fmaf(-ys[q], c0.y, c0.z)));
+    } else if (rem == 2) {
+        const float4 c0 = cs[k], c1 = cs[k + 1];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            m[q] = fmin3_nan(m[q], fmaf(-xs[q], c0.x, fmaf(-ys[q], c0.y, c0.z)),
+                             fmaf(-xs[q], c1.x, fmaf(-ys[q], c1.y, c1.z)));
+    } else if (rem == 3) {
+        const float4 c0 = cs[k], c1 = cs[k + 1], c2 = cs[k + 2];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            m[q] = fmin3_nan(fmin_nan(m[q], fmaf(-xs[q], c0.x, fmaf(-ys[q], c0.y, c0.z))),
+                             fmaf(-xs[q], c1.x, fmaf(-ys[q], c1.y, c1.z)),
+                             fmaf(-xs[q], c2.x, fmaf(-ys[q], c2.y, c2.z)));
+    }
+    uint32_t w_in[PPL];
+    bool unc[PPL];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        // B >= beta0 + beta1 max(|x|, |y|); NaN m or infinite B is never "in"
+        const float B = fmaf(b1, fabsf(xs[q]) + fabsf(ys[q]), b0);
+        const bool in = (m[q] >= B) && (!INT || exin[q]) && valid[q];
+        unc[q] = (!(fabsf(m[q]) >= B) || (INT && !exin[q])) && valid[q];
+        any |= unc[q];
+        w_in[q] = __ballot_sync(0xffffffffu, in);
+    }
+    if (__any_sync(0xffffffffu, any)) {
+        // one reservation in the global queue for the whole slice
+        uint32_t u[PPL];
+        unsigned int total = 0;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            u[q] = __ballot_sync(0xffffffffu, unc[q]);
+            total += (unsigned int)__popc(u[q]);
+        }
+        unsigned int base = 0;
+        if (lane == 0) base = atomicAdd(qcount, total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            if (unc[q]) queue[base + __popc(u[q] & lt)] = (uint32_t)(gs + 32 * q + lane);
+            base += (unsigned int)__popc(u[q]);
+        }
+    }
+    uint32_t *mw = mask + (gs >> 5);
+    if (!TAIL) {
+        if (vec_store && (PPL % 4) == 0) {
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < PPL; q += 4)
+                    *(uint4 *)(mw + q) = make_uint4(w_in[q], w_in[q + 1], w_in[q + 2], w_in[q + 3]);
+            }
+        } else {
+            uint32_t myword = 0;
+#pragma unroll
+            for (int q = 0; q < PPL; ++q)
+                if (lane == q) myword = w_in[q];
+            if (lane < PPL) mw[lane] = myword;
+        }
+    } else {
+        uint32_t myword = 0;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            if (lane == q) myword = w_in[q];
+        if (lane < PPL) {
+            const int64_t w0 = gs + 32 * lane;  // first point of this lane's word
+            if (w0 >= a && w0 + 32 <= b) mw[lane] = myword;        // wholly this polygon's
+            else if (w0 < b && w0 + 32 > a && myword) atomicOr(&mw[lane], myword);  // shared, zeroed
+        }
+    }
+}
+
+// A polygon that failed validation contains no point: its words are zero.
+template <int PPL>
+__device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_t b, int lane,
+                                                   uint32_t *__restrict__ mask)
+{
+    if (lane < PPL) {
+        const int64_t w0 = gs + 32 * lane;
+        if (w0 >= a && w0 + 32 <= b) mask[(gs >> 5) + lane] = 0u;
+    }
+}
+
+template <int PPL, int STAGES, bool INT>
+__global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBlocks) ragged_tma_kernel(
+    const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, const void *__restrict__ pts,
+    const RaggedItem *__restrict__ items, const int64_t *__restrict__ prefix, int P,
+    unsigned int *__restrict__ counters, uint32_t *__restrict__ mask, uint32_t *__restrict__ queue,
+    unsigned int *__restrict__ qcount, int *__restrict__ err)
+{
+    using C = RaggedCfg<PPL, STAGES>;
+    constexpr int kSlice = C::kSlice;
+    constexpr int kTile = C::kTile;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = (uint64_t *)(smem + C::kBarOff);
+    uint64_t *empty = full + STAGES;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kRaggedWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kRaggedWarps) {
+        // ---------------- producer: one lane takes items and issues the copies
+        if (lane == 0) {
+            // items are taken two ahead of the one being issued, so that the
+            // counter's round trip and the item row's load overlap the waits
+            const int64_t total = prefix[P];
+            auto grab = [&](int64_t prev) -> int64_t {
+                return prev < total ? (int64_t)atomicAdd(&counters[0], 1u) : total;
+            };
+            int64_t cur = grab(0);
+            int64_t nxt = grab(cur);
+            RaggedItem ci{};
+            if (cur < total) ci = items[cur];
+            int it = 0, s = 0;
+            uint32_t ephase = 0;
+            int rot = 0;
+            bool fail = false;
+            for (;; ++it) {
+                const int64_t after = grab(nxt);
+                RaggedItem ni{};
+                if (nxt < total) ni = items[nxt];
+                if (it >= STAGES && !mbar_wait(&empty[s], ephase, err)) {
+                    fail = true;
+                    break;
+                }
+                unsigned char *st = smem + (size_t)s * C::kStageBytes;
+                RaggedHeader *h = (RaggedHeader *)(st + C::kHdrOff);
+                if (cur >= total) {
+                    h->j = -1;
+                    mbar_arrive(&full[s]);  // release: the header is visible to the consumers
+                    break;
+                }
+                const int64_t c0 = (int64_t)ci.k * kTile;
+                const int64_t sa = (c0 + ci.lo) & ~(int64_t)1, eb = (c0 + ci.hi) & ~(int64_t)1;
+                const uint32_t pbytes = eb > sa ? (uint32_t)((eb - sa) * 8) : 0u;
+                h->j = ci.j;
+                h->k = ci.k;
+                h->lo = ci.lo;
+                h->hi = ci.hi;
+                h->rot = rot;
+                rot = (rot + (ci.hi - 1) / kSlice - ci.lo / kSlice + 1) & (kRaggedWarps - 1);
+                const uint32_t cbytes = (uint32_t)(kPadStride * sizeof(float4));
+                mbar_arrive_expect_tx(&full[s], pbytes + cbytes + (uint32_t)sizeof(PolyInfo));
+                if (pbytes) bulk_copy_g2s(st + (sa - c0) * 8, (const char *)pts + sa * 8, pbytes, &full[s]);
+                bulk_copy_g2s(st + C::kCoefOff, coefp + (size_t)ci.j * kPadStride, cbytes, &full[s]);
+                bulk_copy_g2s(st + C::kInfoOff, poly + ci.j, (uint32_t)sizeof(PolyInfo), &full[s]);
+                cur = nxt;
+                nxt = after;
+                ci = ni;
+                if (++s == STAGES) {
+                    s = 0;
+                    if (it + 1 >= 2 * STAGES) ephase ^= 1u;
+                }
+            }
+            if (fail) {
+                // gave up: let the copies already issued land before the CTA leaves
+                for (int k = it > STAGES ? it - STAGES : 0; k < it; ++k)
+                    mbar_wait(&full[k % STAGES], (uint32_t)((k / STAGES) & 1), err);
+            }
+        }
+    } else {
+        // ---------------- consumers
+        const bool vec_store = ((uintptr_t)mask & 15) == 0;
+        int s = 0;
+        uint32_t fphase = 0;
+        for (;;) {
+            if (!mbar_wait(&full[s], fphase, err)) break;
+            const unsigned char *st = smem + (size_t)s * C::kStageBytes;
+            const RaggedHeader h = *(const RaggedHeader *)(st + C::kHdrOff);
+            if (h.j < 0) break;
+            const int nsl = (h.hi - 1) / kSlice - h.lo / kSlice + 1;
+            const int r = (warp - h.rot) & (kRaggedWarps - 1);
+            if (r < nsl) {
+                const PolyInfo &pi = *(const PolyInfo *)(st + C::kInfoOff);
+                const int64_t c0 = (int64_t)h.k * kTile;
+                const int sl = h.lo / kSlice + r;
+                const int64_t gs = c0 + (int64_t)sl * kSlice;
+                const int64_t a = c0 + h.lo, b = c0 + h.hi;
+                const unsigned char *rows = st + (size_t)sl * kSlice * 8;
+                const float4 *cs = (const float4 *)(st + C::kCoefOff);
+                const bool whole = gs >= a && gs + kSlice <= b;
+                if (pi.status != PIP_OK) {
+                    ragged_slice_empty<PPL>(gs, a, b, lane, mask);
+                } else if (whole) {
+                    if (pi.ox == 0.f && pi.oy == 0.f)
+                        ragged_slice<PPL, INT, false, false>(cs, pi.n, 0.f, 0.f, pi.beta0, pi.beta1, rows, pts, gs,
+                                                             a, b, lane, mask, vec_store, queue, qcount);
+                    else
+                        ragged_slice<PPL, INT, true, false>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts,
+                                                            gs, a, b, lane, mask, vec_store, queue, qcount);
+                } else {
+                    ragged_slice<PPL, INT, true, true>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts, gs,
+                                                       a, b, lane, mask, vec_store, queue, qcount);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (++s == STAGES) {
+                s = 0;
+                fphase ^= 1u;
+            }
+        }
+    }
+}
+
+}  // namespace

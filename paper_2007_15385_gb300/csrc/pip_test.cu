@@ -24,6 +24,7 @@ using namespace pip;
 
 #include "pip_test_kernels.cuh"
 #include "pip_stream_tma.cuh"
+#include "pip_ragged_tma.cuh"
 
 namespace {
 
@@ -51,6 +52,32 @@ cudaError_t launch_ragged(const pip_tables *t, const void *pts, int64_t M, const
     k<<<blocks_for(k, t->num_sms, kThreads), kThreads, 0, s>>>(t->d_poly, t->d_coef, pts, M, poffs, t->P,
                                                      t->d_items, kItemChunks, t->d_work, mask,
                                                      t->d_queue, t->d_qcount);
+    return cudaGetLastError();
+}
+
+// The pipelined own-polygon batch: setup (items, shared mask words, counters)
+// then the persistent kernel; 12 points a lane, three stages.
+constexpr int kRaggedPPL = 12;
+constexpr int kRaggedStages = 3;
+
+template <bool INT>
+cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
+                              uint32_t *mask, cudaStream_t s)
+{
+    using C = RaggedCfg<kRaggedPPL, kRaggedStages>;
+    ragged_items_kernel<<<1, 1024, 0, s>>>(poffs, t->P, M, C::kTile, t->d_items, (RaggedItem *)t->d_ritems,
+                                           t->ritems_cap, t->d_work, t->d_qcount, t->d_worst, mask);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto k = ragged_tma_kernel<kRaggedPPL, kRaggedStages, INT>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRaggedThreads, C::kSmem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    k<<<per_sm * t->num_sms, kRaggedThreads, C::kSmem, s>>>(t->d_poly, t->d_coefp, pts,
+                                                            (const RaggedItem *)t->d_ritems, t->d_items, t->P,
+                                                            t->d_work, mask, t->d_queue, t->d_qcount, t->d_error);
     return cudaGetLastError();
 }
 
@@ -409,6 +436,17 @@ cudaError_t stream_kernels_setup()
 
 int stream_variant_count() { return kNumStreamVariants; }
 
+cudaError_t ragged_kernels_setup()
+{
+    const int bytes = (int)RaggedCfg<kRaggedPPL, kRaggedStages>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(ragged_tma_kernel<kRaggedPPL, kRaggedStages, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tma_kernel<kRaggedPPL, kRaggedStages, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 cudaError_t allpairs_setup()
 {
     cudaError_t e = cudaFuncSetAttribute(allpairs_split_kernel<false>,
@@ -460,9 +498,11 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
             PIP_CUDA_TRY(cudaMemsetAsync(t->d_qcount, 0, sizeof(unsigned int), s));
             return PIP_OK;
         }
-        if (ints) e = v16 ? launch_ragged<true, true>(t, d_points, num_points, d_point_offsets, mask, s)
-                          : launch_ragged<true, false>(t, d_points, num_points, d_point_offsets, mask, s);
-        else e = v16 ? launch_ragged<false, true>(t, d_points, num_points, d_point_offsets, mask, s)
+        if (v16)  // bulk copies want a 16-byte aligned point array
+            e = ints ? launch_ragged_tma<true>(t, d_points, num_points, d_point_offsets, mask, s)
+                     : launch_ragged_tma<false>(t, d_points, num_points, d_point_offsets, mask, s);
+        else
+            e = ints ? launch_ragged<true, false>(t, d_points, num_points, d_point_offsets, mask, s)
                      : launch_ragged<false, false>(t, d_points, num_points, d_point_offsets, mask, s);
     } else if (t->P == 1 && !want_hit && v16 && t->have_host_poly) {
         // the pipelined kernel: bulk test and exact refine in one launch

@@ -133,6 +133,47 @@ def test_gis_batch_with_empty_and_tiny_polygons():
     assert_same(got, oracle_own(w), "gis tiny")
 
 
+def test_gis_batch_unaligned_points():
+    # points 8 bytes past a 16-byte boundary: the batch runs without bulk copies
+    w = wl.gis_batch(seed=17, num_polygons=48, m_range=(10, 3000))
+    got, _, _, st = run_test(w, points_offset=1)
+    assert st == B.PIP_OK
+    assert_same(got, oracle_own(w), "gis unaligned")
+
+
+def test_ragged_invalid_polygons_hold_nothing():
+    sq = [[0, 0], [4, 0], [4, 4], [0, 4]]
+    polys = [sq, [[0, 0], [2, 0], [1, 0.2], [2, 2], [0, 2]], [[0, 0], [1, 0], [2, 0]], sq,
+             [[0, 0], [1, 0], [1, 0], [0, 1]], sq]
+    verts = np.concatenate([np.array(p, np.float32) for p in polys])
+    voffs = np.zeros(len(polys) + 1, np.int32)
+    voffs[1:] = np.cumsum([len(p) for p in polys])
+    rng = np.random.default_rng(18)
+    counts = [5000, 37, 4100, 3, 900, 6000]  # shared mask words between neighbours
+    poffs = np.zeros(len(polys) + 1, np.int64)
+    poffs[1:] = np.cumsum(counts)
+    pts = rng.uniform(-1, 5, size=(int(poffs[-1]), 2)).astype(np.float32)
+    w = wl.Workload("invalid_ragged", verts, voffs, pts, poffs)
+    got, _, _, st = run_test(w)
+    want = oracle_own(w)
+    assert_same(got, want, "ragged invalid")
+    for j in (1, 2, 4):
+        assert not got[poffs[j]:poffs[j + 1]].any()
+
+
+def test_ragged_offsets_that_do_not_cover_the_points_are_rejected():
+    w = wl.gis_batch(seed=19, num_polygons=8, m_range=(100, 400))
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    bad = w.point_offsets.copy()
+    bad[-1] -= 1  # the last offset must be the number of points
+    B.pip_test(t, torch.from_numpy(w.points).to(dev()), torch.from_numpy(bad).to(dev()))
+    worst, _ = B.pip_get_status(t)
+    assert worst == B.PIP_E_INVALID_ARG
+    t.close()
+
+
 def test_all_pairs_first_hit_small():
     w = wl.gis_all_pairs(seed=14, num_polygons=96, m=30_011, total_polygons=96)
     got, fh, refine, st = run_test(w, mode=B.PIP_MASK | B.PIP_FIRST_HIT)
