@@ -177,6 +177,29 @@ def run_reference(args):
     return 0
 
 
+def dist_env() -> tuple[int, int, int]:
+    """(world size, rank, local rank) as torchrun sets them; (1, 0, 0) alone."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x of all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Weak scaling: every rank decides its own shard of units; the job's
+    rate is all ranks' units over the slowest rank's time, in G units/s."""
+    return units_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,15 +235,14 @@ def main():
     from paper_2007_15385_gb300 import binding as B
     from paper_2007_15385_gb300 import workloads as wl
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = wl.vehicle_footprint(m=args.points)
+    # each rank decides its own shard of points against the same footprint
+    w = wl.vehicle_footprint(m=args.points, shard=rank)
     M = w.num_points
     n = int(w.edges()[0])
     v = torch.from_numpy(w.vertices).to(dev)
@@ -234,13 +256,6 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        tt = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
 
     stream = torch.cuda.current_stream()
     # tile shape of the pipelined kernel, tuned on this workload (not timed)
@@ -273,7 +288,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms_total = max_over_ranks(ev0.elapsed_time(ev1))
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     calls, bulk_ms, refine_ms = B.pip_timing_read(t)
     B.pip_timing(t, False)
     _, refine_count = B.pip_get_status(t)
@@ -281,7 +296,7 @@ def main():
     # the pipelined path (16-byte aligned points) is one kernel per step
     calls_launches = 1 if p.data_ptr() % 16 == 0 else 2
     tests_per_step = M * n
-    value = tests_per_step * world / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(tests_per_step, world, ms_step)
 
     # roofline of the dominant (bulk streaming) kernel
     bytes_per_launch = M * 8 + ((M + 31) // 32) * 4
@@ -305,8 +320,8 @@ def main():
         B.pip_test_host(t, p_host, p, mask, mask_host)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / e2e_steps
-    e2e_value = tests_per_step * world / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / e2e_steps
+    e2e_value = whole_job_rate(tests_per_step, world, e2e_ms)
 
     # same-chip comparators on the same workload (Alg. 2, Alg. 1, plain fp64 Alg. 5)
     comparators = {}

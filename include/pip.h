@@ -50,7 +50,7 @@ typedef enum {
     PIP_E_NONCONVEX = 3,   /* turns both ways, folds back, or winds more than once */
     PIP_E_NONFINITE = 4,   /* NaN or infinite vertex coordinate */
     PIP_E_CUDA = 5,        /* a CUDA runtime call failed */
-    PIP_E_TIMEOUT = 6,     /* reserved: a bounded device-side wait ran out */
+    PIP_E_TIMEOUT = 6,     /* a bounded device-side wait ran out (see pip_selftest_wait_timeout) */
     PIP_E_CAPACITY = 7     /* more points than the capacity given to pip_prepare */
 } pip_status;
 
@@ -296,6 +296,26 @@ pip_status pip_penalty_backward(const float *d_vertices, int32_t num_vertices, c
 pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype vdtype, int32_t num_vertices,
                                    const void *d_points, pip_dtype pdtype, int64_t num_points,
                                    uint32_t *d_mask, int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------------
+ * pip_selftest_wait_timeout -- the paper has no counterpart to this call; it
+ * exercises the failure path that every pipelined kernel takes when one of
+ * its waits never completes (a lost producer or consumer).
+ *
+ * Launches one CTA that starts a 4 KiB bulk copy into shared memory, then
+ * waits on an mbarrier phase that nothing completes, bounded by
+ * `limit_cycles` SM cycles (1 .. 2^31; the kernels' own limit is 2e9, about
+ * a second).  When the limit runs out the kernel records PIP_E_TIMEOUT in the
+ * tables' error word, waits (again bounded) for its own copy to land and
+ * returns: no trap, no fault, the context stays usable.  The next
+ * pip_get_status returns PIP_E_TIMEOUT once and clears the word.
+ *
+ *   t         tables from pip_prepare (only the error word is written)
+ *   d_scratch device, >= 4096 bytes, 16-byte aligned (the copy's source)
+ * Returns PIP_OK when the launch was queued, PIP_E_INVALID_ARG or PIP_E_CUDA.
+ * ------------------------------------------------------------------------ */
+pip_status pip_selftest_wait_timeout(pip_tables *t, const void *d_scratch, int64_t limit_cycles,
+                                     void *stream);
 
 #ifdef __cplusplus
 }

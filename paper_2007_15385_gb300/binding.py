@@ -53,6 +53,7 @@ SIGNATURES = {
     "pip_test_voronoi_fp64": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "pip_test_single_noalloc": (_INT, [_P, _INT, _I32, _P, _INT, _I64, _P, _P, _P]),
     "pip_stream_variant_count": (_I32, []),
+    "pip_selftest_wait_timeout": (_INT, [_P, _P, _I64, _P]),
     "pip_penalty_workspace_bytes": (ctypes.c_size_t, [_I32, _I32, _I64]),
     "pip_penalty_forward": (_INT, [_P, _I32, _P, _I32, _P, _I64, ctypes.c_float, _P, _P,
                                     ctypes.c_size_t, _P]),
@@ -318,6 +319,15 @@ def pip_test_host(tables: Tables, points_host: torch.Tensor, device_points: torc
 
 
 NOALLOC_MAX_POINTS = 1 << 20
+
+
+def pip_selftest_wait_timeout(tables: Tables, limit_cycles: int, stream=None) -> None:
+    """Queue the self-test of a device-side wait that never completes (bounded by
+    ``limit_cycles`` SM cycles); the next pip_get_status reports PIP_E_TIMEOUT."""
+    scratch = torch.zeros(4096, dtype=torch.uint8, device=tables.device)
+    _check(lib().pip_selftest_wait_timeout(tables, scratch.data_ptr(), int(limit_cycles), _stream(stream)),
+           "pip_selftest_wait_timeout")
+    tables._keep = scratch  # the copy reads it until the kernel ends
 
 
 def pip_test_single_noalloc(vertices: torch.Tensor, points: torch.Tensor, mask: torch.Tensor,

@@ -128,7 +128,7 @@ extern "C" pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype 
 #undef NOALLOC_STREAM
     PIP_CUDA_TRY(cudaGetLastError());
 
-    RefineArgs A;
+    RefineArgs A{};
     A.poly = &s->poly;
     A.coef = s->coef;
     A.g0 = &s->g0;
@@ -144,7 +144,7 @@ extern "C" pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype 
     A.qcount = &s->qcount;
     A.mask = d_mask;
     A.first_hit = nullptr;
-    refine_kernel<<<num_sms * 2, kThreads, 0, cs>>>(A, kSingle);
+    refine_kernel<false><<<num_sms * 2, kThreads, 0, cs>>>(A, kSingle);
     PIP_CUDA_TRY(cudaGetLastError());
     return PIP_OK;
 }

@@ -129,14 +129,16 @@ __global__ void __launch_bounds__(1024) ragged_items_kernel(
 }
 
 // One consumer warp, one slice: points gs + [0, 32*PPL) of which [a, b) are
-// this polygon's (TAIL: the slice is not wholly inside; the odd last point of
-// the range is not in the bulk copy and is read from global memory).
+// polygon j's (TAIL: the slice is not wholly inside; the odd last point of
+// the range is not in the bulk copy and is read from global memory).  An
+// uncertain point is queued with its polygon (queue / qpoly).
 template <int PPL, bool INT, bool CENTER, bool TAIL>
 __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, float oy, float b0, float b1,
                                              const unsigned char *rows, const void *__restrict__ pts,
                                              int64_t gs, int64_t a, int64_t b, int lane,
-                                             uint32_t *__restrict__ mask, bool vec_store,
-                                             uint32_t *__restrict__ queue, unsigned int *__restrict__ qcount)
+                                             uint32_t *__restrict__ mask, bool vec_store, int j,
+                                             uint32_t *__restrict__ queue, uint32_t *__restrict__ qpoly,
+                                             unsigned int *__restrict__ qcount)
 {
     float xs[PPL], ys[PPL], m[PPL];
     bool exin[PPL], valid[PPL];
@@ -236,7 +238,11 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
         const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
-            if (unc[q]) queue[base + __popc(u[q] & lt)] = (uint32_t)(gs + 32 * q + lane);
+            if (unc[q]) {
+                const unsigned int at = base + __popc(u[q] & lt);
+                queue[at] = (uint32_t)(gs + 32 * q + lane);
+                qpoly[at] = (uint32_t)j;
+            }
             base += (unsigned int)__popc(u[q]);
         }
     }
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBl
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, const void *__restrict__ pts,
     const RaggedItem *__restrict__ items, const int64_t *__restrict__ prefix, int P,
     unsigned int *__restrict__ counters, uint32_t *__restrict__ mask, uint32_t *__restrict__ queue,
-    unsigned int *__restrict__ qcount, int *__restrict__ err)
+    uint32_t *__restrict__ qpoly, unsigned int *__restrict__ qcount, int *__restrict__ err)
 {
     using C = RaggedCfg<PPL, STAGES>;
     constexpr int kSlice = C::kSlice;
@@ -388,13 +394,13 @@ __global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBl
                 } else if (whole) {
                     if (pi.ox == 0.f && pi.oy == 0.f)
                         ragged_slice<PPL, INT, false, false>(cs, pi.n, 0.f, 0.f, pi.beta0, pi.beta1, rows, pts, gs,
-                                                             a, b, lane, mask, vec_store, queue, qcount);
+                                                             a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
                     else
                         ragged_slice<PPL, INT, true, false>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts,
-                                                            gs, a, b, lane, mask, vec_store, queue, qcount);
+                                                            gs, a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
                 } else {
                     ragged_slice<PPL, INT, true, true>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts, gs,
-                                                       a, b, lane, mask, vec_store, queue, qcount);
+                                                       a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
                 }
             }
             __syncwarp();

@@ -77,7 +77,8 @@ cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, c
     if (per_sm > 2) per_sm = 2;
     k<<<per_sm * t->num_sms, kRaggedThreads, C::kSmem, s>>>(t->d_poly, t->d_coefp, pts,
                                                             (const RaggedItem *)t->d_ritems, t->d_items, t->P,
-                                                            t->d_work, mask, t->d_queue, t->d_qcount, t->d_error);
+                                                            t->d_work, mask, t->d_queue, t->d_keys, t->d_qcount,
+                                                            t->d_error);
     return cudaGetLastError();
 }
 
@@ -275,12 +276,9 @@ cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int
     return cudaGetLastError();
 }
 
-// Warp-cooperative refine for float inputs and for the all-pairs test: one
-// warp per queued point.  Own-polygon or single mode: the lanes split the
-// polygon's edges (warp_inside_exact).  All pairs: the lanes take 32
-// polygons at a time and make the float32 decision of each; the lowest
-// polygon that is decided inside, or is uncertain and then found inside
-// exactly, is the first hit.
+// Warp-cooperative refine for float inputs: one warp per queued point, the
+// lanes split the polygon's edges (warp_inside_exact).  Own-polygon mode takes
+// the polygon from the queue (or from the offsets); single mode has one.
 __global__ void __launch_bounds__(kThreads) refine_warp_kernel(RefineArgs A, int mode)
 {
     const int lane = threadIdx.x & 31;
@@ -288,46 +286,63 @@ __global__ void __launch_bounds__(kThreads) refine_warp_kernel(RefineArgs A, int
     const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (unsigned int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < count; q += nwarps) {
         const int64_t i = A.queue[q];
-        if (mode == kAllPairs) {
-            // the lowest candidate is uncertain: scan upward from it
-            const int start = (int)(A.keys[i] >> 1);
-            const int limit = A.P;
-            int hit = -1;
-            for (int base = start; base < limit; base += 32) {
-                const int j = base + lane;
-                const int b = j < limit ? bulk_decision(A, j, i) : -1;
-                const uint32_t in_m = __ballot_sync(0xffffffffu, b > 0);
-                uint32_t cand = in_m | __ballot_sync(0xffffffffu, b == 0);
-                bool found = false;
-                while (cand) {
-                    const int l = __ffs(cand) - 1;
-                    cand &= cand - 1;
-                    if (((in_m >> l) & 1u) ||
-                        warp_inside_exact(A.poly, base + l, A.g0, A.gk, A.verts, A.vdtype, A.pts, A.pdtype, i)) {
-                        hit = base + l;
-                        found = true;
-                        break;
-                    }
-                }
-                if (found) break;
+        int j = 0;
+        if (mode == kRagged && A.qpoly) {
+            j = (int)A.qpoly[q];
+        } else if (mode == kRagged) {
+            int lo = 0, hi = A.P;  // poffs[lo] <= i < poffs[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (A.poffs[mid] <= i) lo = mid; else hi = mid;
             }
-            if (lane == 0) {
-                if (A.first_hit) A.first_hit[i] = hit;
-                if (A.mask && hit >= 0) atomicOr(&A.mask[i >> 5], 1u << (i & 31));
-            }
-        } else {
-            int j = 0;
-            if (mode == kRagged) {
-                int lo = 0, hi = A.P;  // poffs[lo] <= i < poffs[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (A.poffs[mid] <= i) lo = mid; else hi = mid;
-                }
-                j = lo;
-            }
-            if (warp_inside_exact(A.poly, j, A.g0, A.gk, A.verts, A.vdtype, A.pts, A.pdtype, i) && lane == 0)
-                atomicOr(&A.mask[i >> 5], 1u << (i & 31));
+            j = lo;
         }
+        if (warp_inside_exact(A.poly, j, A.g0, A.gk, A.verts, A.vdtype, A.pts, A.pdtype, i) && lane == 0)
+            atomicOr(&A.mask[i >> 5], 1u << (i & 31));
+    }
+}
+
+// All-pairs refine, one block per queued point: warp w scans polygons
+// start + 32 w + 256 r upward (float32 decision per lane, exact test by the
+// whole warp for uncertain ones) and stops at its first hit or once it has
+// passed the lowest hit any warp has found; that lowest hit is the answer.
+__global__ void __launch_bounds__(kThreads) refine_allpairs_kernel(RefineArgs A)
+{
+    __shared__ int best;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kStride = kThreads;  // polygons per round of the whole block
+    const unsigned int count = *A.qcount;
+    for (unsigned int q = blockIdx.x; q < count; q += gridDim.x) {
+        const int64_t i = A.queue[q];
+        if (threadIdx.x == 0) best = INT_MAX;
+        __syncthreads();
+        const int start = (int)(A.keys[i] >> 1);
+        for (int base = start + 32 * warp; base < A.P; base += kStride) {
+            if (base > *(volatile int *)&best) break;
+            const int j = base + lane;
+            const int b = j < A.P ? bulk_decision(A, j, i) : -1;
+            const uint32_t in_m = __ballot_sync(0xffffffffu, b > 0);
+            uint32_t cand = in_m | __ballot_sync(0xffffffffu, b == 0);
+            bool found = false;
+            while (cand) {
+                const int l = __ffs(cand) - 1;
+                cand &= cand - 1;
+                if (((in_m >> l) & 1u) ||
+                    warp_inside_exact(A.poly, base + l, A.g0, A.gk, A.verts, A.vdtype, A.pts, A.pdtype, i)) {
+                    if (lane == 0) atomicMin(&best, base + l);
+                    found = true;
+                    break;
+                }
+            }
+            if (found) break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int hit = best == INT_MAX ? -1 : best;
+            if (A.first_hit) A.first_hit[i] = hit;
+            if (A.mask && hit >= 0) atomicOr(&A.mask[i >> 5], 1u << (i & 31));
+        }
+        __syncthreads();  // best is reset for the next point
     }
 }
 
@@ -533,7 +548,7 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     if (e != cudaSuccess) return PIP_E_CUDA;
     timing_mark(t, 1, s);
 
-    RefineArgs A;
+    RefineArgs A{};
     A.poly = t->d_poly;
     A.coef = t->d_coef;
     A.g0 = t->d_g0;
@@ -550,8 +565,12 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     A.mask = mask;
     A.first_hit = hit;
     A.keys = t->d_keys;
+    // the pipelined batch kernel files the polygon of each queued point in the keys buffer
+    A.qpoly = (kmode == kRagged && v16) ? t->d_keys : nullptr;
     if (kmode != kAllPairs && t->vdtype == PIP_I32 && pdtype == PIP_I32)
-        refine_kernel<<<t->num_sms * 2, kThreads, 0, s>>>(A, kmode);  // int64, one thread a point
+        refine_kernel<true><<<t->num_sms * 8, kThreads, 0, s>>>(A, kmode);  // int64, one thread a point
+    else if (kmode == kAllPairs)
+        refine_allpairs_kernel<<<t->num_sms * 2, kThreads, 0, s>>>(A);
     else
         refine_warp_kernel<<<t->num_sms * 4, kThreads, 0, s>>>(A, kmode);
     if (cudaGetLastError() != cudaSuccess) return PIP_E_CUDA;

@@ -290,6 +290,7 @@ struct RefineArgs {
     uint32_t *mask;
     int32_t *first_hit;
     const uint32_t *keys;  // all-pairs candidate keys (pip_test's split path)
+    const uint32_t *qpoly; // own-polygon batch: the polygon of each queued point, or null
 };
 
 __device__ __forceinline__ void vertex_d(const void *verts, int vdtype, int64_t i, double &x, double &y)
@@ -305,6 +306,24 @@ __device__ __forceinline__ void vertex_d(const void *verts, int vdtype, int64_t 
     }
 }
 
+// Integer polygon and point: every edge's orientation in int64 (exact),
+// the point inside iff none has the opposite sign of the polygon's turn.
+__device__ __forceinline__ bool inside_exact_int(const RefineArgs &A, int n, int v0, int sigma, int64_t i)
+{
+    const int2 pq = ((const int2 *)A.pts)[i];
+    const int64_t px = pq.x, py = pq.y;
+    const int2 *v = (const int2 *)A.verts + v0;
+    int2 a = v[n - 1];
+    for (int k = 0; k < n; ++k) {
+        const int2 b = v[k];
+        // |b - a| <= 2^25 and |p - a| < 2^32 + 2^24: each product < 2^58
+        const int64_t cr = (int64_t)(b.x - (int64_t)a.x) * (py - a.y) - (int64_t)(b.y - (int64_t)a.y) * (px - a.x);
+        if ((cr > 0 ? 1 : (cr < 0 ? -1 : 0)) == -sigma) return false;
+        a = b;
+    }
+    return true;
+}
+
 // Exact inclusion of point i in polygon j: fp64 Voronoi first (Alg. 5 with
 // the stored generators, decided where the fp64 bound allows), exact
 // orientation for the edges it leaves open.
@@ -313,20 +332,7 @@ __device__ bool inside_exact(const RefineArgs &A, int j, int64_t i)
     const PolyInfo pi = A.poly[j];
     if (pi.status != PIP_OK) return false;
     const int n = pi.n, v0 = pi.voff, sigma = pi.orient;
-    if (A.vdtype == PIP_I32 && A.pdtype == PIP_I32) {
-        const int32_t *q = (const int32_t *)A.pts;
-        const int64_t px = q[2 * i], py = q[2 * i + 1];
-        const int32_t *v = (const int32_t *)A.verts;
-        for (int k = 0; k < n; ++k) {
-            const int km = k == 0 ? n - 1 : k - 1;
-            const int64_t ax = v[2 * (v0 + km)], ay = v[2 * (v0 + km) + 1];
-            const int64_t bx = v[2 * (v0 + k)], by = v[2 * (v0 + k) + 1];
-            // |b - a| <= 2^25 and |p - a| < 2^32 + 2^24: each product < 2^58
-            const int64_t cr = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
-            if ((cr > 0 ? 1 : (cr < 0 ? -1 : 0)) == -sigma) return false;
-        }
-        return true;
-    }
+    if (A.vdtype == PIP_I32 && A.pdtype == PIP_I32) return inside_exact_int(A, n, v0, sigma, i);
     double px, py;
     vertex_d(A.pts, A.pdtype, i, px, py);
     if (!isfinite(px) || !isfinite(py)) return false;
@@ -374,34 +380,35 @@ __device__ int bulk_decision(const RefineArgs &A, int j, int64_t i)
     return d.in ? 1 : (d.unc ? 0 : -1);
 }
 
+// One thread per queued point, single or own-polygon mode.  INT: integer
+// polygons and points (the int64 test is short and needs no lane
+// cooperation; a small kernel keeps many threads resident to hide the loads).
+template <bool INT>
 __global__ void __launch_bounds__(kThreads) refine_kernel(RefineArgs A, int mode)
 {
     const unsigned int count = *A.qcount;
     for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < count;
          q += gridDim.x * blockDim.x) {
         const int64_t i = A.queue[q];
-        if (mode == kAllPairs) {
-            const int c = A.first_hit ? A.first_hit[i] : -1;
-            const int limit = c < 0 ? A.P : c;
-            int hit = c;
-            for (int j = 0; j < limit; ++j) {
-                const int b = bulk_decision(A, j, i);
-                if (b > 0 || (b == 0 && inside_exact(A, j, i))) { hit = j; break; }
+        int j = 0;
+        if (mode == kRagged && A.qpoly) {
+            j = (int)A.qpoly[q];
+        } else if (mode == kRagged) {
+            int lo = 0, hi = A.P;  // poffs[lo] <= i < poffs[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (A.poffs[mid] <= i) lo = mid; else hi = mid;
             }
-            if (A.first_hit) A.first_hit[i] = hit;
-            if (A.mask && hit >= 0) atomicOr(&A.mask[i >> 5], 1u << (i & 31));
-        } else {
-            int j = 0;
-            if (mode == kRagged) {
-                int lo = 0, hi = A.P;  // poffs[lo] <= i < poffs[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (A.poffs[mid] <= i) lo = mid; else hi = mid;
-                }
-                j = lo;
-            }
-            if (inside_exact(A, j, i)) atomicOr(&A.mask[i >> 5], 1u << (i & 31));
+            j = lo;
         }
+        bool in;
+        if (INT) {
+            const PolyInfo *pi = A.poly + j;
+            in = pi->status == PIP_OK && inside_exact_int(A, pi->n, pi->voff, pi->orient, i);
+        } else {
+            in = inside_exact(A, j, i);
+        }
+        if (in) atomicOr(&A.mask[i >> 5], 1u << (i & 31));
     }
 }
 

@@ -54,9 +54,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for the phase with the given parity to complete; false on timeout
-// (PIP_E_TIMEOUT recorded in *err).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err)
+// Waits for the phase with the given parity to complete; false once `limit`
+// SM cycles have passed (PIP_E_TIMEOUT recorded in *err).
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity, int *err, long long limit)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
@@ -64,11 +64,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
         // the clock is read once per 64 tries, so that waiting costs few issue slots
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             atomicExch(err, (int)PIP_E_TIMEOUT);
             return false;
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err)
+{
+    return mbar_wait_limit(bar, parity, err, kWaitCycles);
 }
 
 // bytes (multiple of 16) from 16-byte aligned global src to 16-byte aligned

@@ -110,10 +110,14 @@ def unit_circle_octagon(seed: int = 0, m: int = 100_000, n: int = 8) -> Workload
     return Workload("unit_circle_octagon", v, np.array([0, n], np.int32), pts)
 
 
-def vehicle_footprint(seed: int = 1, m: int = 1 << 26, n: int = 12) -> Workload:
+def vehicle_footprint(seed: int = 1, m: int = 1 << 26, n: int = 12, shard: int = 0) -> Workload:
+    """One footprint against m LiDAR-like points.  ``shard`` r > 0 keeps the
+    footprint and draws its own points (one rank's share of a larger job);
+    shard 0 is the single-GPU workload itself."""
     rng = np.random.default_rng(seed)
     v = _circle_polygon(rng, n, 0.0, 0.0, 2.4, 1.0)
-    pts = _lidar_points(rng, m, -20.0, 20.0)
+    prng = rng if shard == 0 else np.random.default_rng([seed, 1000 + shard])
+    pts = _lidar_points(prng, m, -20.0, 20.0)
     return Workload("vehicle_footprint", v, np.array([0, n], np.int32), pts)
 
 
