@@ -447,15 +447,31 @@ def run_other(args):
         mask = torch.empty((M + 31) // 32, dtype=torch.int32, device=dev)
         hit = torch.empty(M, dtype=torch.int32, device=dev) if mode & B.PIP_FIRST_HIT else None
         call = lambda: B.pip_test(t, p, po, mode=mode, mask=mask, first_hit=hit)
+        extra = {}
+        if po is not None and p.data_ptr() % 16 == 0:
+            # tile shape of the pipelined batch kernel, tuned on this batch (not timed)
+            extra["batch_variant"], _ = B.pip_autotune_batch(t, p, po, mask, reps=3)
         for _ in range(args.warmup):
             call()
         torch.cuda.synchronize()
         B.pip_timing(t, True)
         ms = time_steps(call, args.steps, 0, stream)
         calls, bulk_ms, refine_ms = B.pip_timing_read(t)
+        B.pip_timing(t, False)
         _, refined = B.pip_get_status(t)
-        extra = {"bulk_kernel_ms": bulk_ms / max(1, calls), "refine_kernel_ms": refine_ms / max(1, calls),
-                 "refined_points_per_step": refined, "refine_fraction": refined / max(1, M)}
+        extra.update({"bulk_kernel_ms": bulk_ms / max(1, calls), "refine_kernel_ms": refine_ms / max(1, calls),
+                      "refined_points_per_step": refined, "refine_fraction": refined / max(1, M)})
+        # the whole call (setup, bulk, refine) captured once as a CUDA graph, replayed per step
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            call()
+        stream.wait_stream(gs)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            call()
+        extra["graph_ms_per_step"] = time_steps(graph.replay, args.steps, 3, stream)
         launches = 3 if po is not None else (1 if (len(w.vertex_offsets) == 2 and p.data_ptr() % 16 == 0) else 2)
         t.close()
     clk = clocks.stop()

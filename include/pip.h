@@ -196,6 +196,21 @@ pip_status pip_autotune_stream(pip_tables *t, const void *d_points, pip_dtype pd
                                int64_t num_points, uint32_t *d_mask, int32_t reps, void *stream,
                                int32_t *best_variant, float *best_ms);
 
+/*
+ * Tile shapes of the pipelined own-polygon batch kernel (the path pip_test
+ * takes with point offsets and 16-byte aligned points): each variant is
+ * (points per lane, ring stages); an item of work is 256 x points per lane
+ * points of one polygon.  pip_autotune_batch times every variant `reps` times
+ * with CUDA events on the caller's own batch (d_point_offsets as in pip_test;
+ * synchronizes, not during capture), keeps the fastest in the tables and
+ * returns it with its mean milliseconds per pip_test call.
+ */
+int32_t pip_batch_variant_count(void);
+pip_status pip_set_batch_variant(pip_tables *t, int32_t variant);
+pip_status pip_autotune_batch(pip_tables *t, const void *d_points, pip_dtype pdtype,
+                              int64_t num_points, const int64_t *d_point_offsets, uint32_t *d_mask,
+                              int32_t reps, void *stream, int32_t *best_variant, float *best_ms);
+
 /* Number of polygons / vertices held by the tables. */
 int32_t pip_num_polygons(const pip_tables *t);
 int32_t pip_total_vertices(const pip_tables *t);

@@ -54,6 +54,10 @@ SIGNATURES = {
     "pip_test_single_noalloc": (_INT, [_P, _INT, _I32, _P, _INT, _I64, _P, _P, _P]),
     "pip_stream_variant_count": (_I32, []),
     "pip_selftest_wait_timeout": (_INT, [_P, _P, _I64, _P]),
+    "pip_batch_variant_count": (_I32, []),
+    "pip_set_batch_variant": (_INT, [_P, _I32]),
+    "pip_autotune_batch": (_INT, [_P, _P, _INT, _I64, _P, _P, _I32, _P, ctypes.POINTER(_I32),
+                                  ctypes.POINTER(ctypes.c_float)]),
     "pip_penalty_workspace_bytes": (ctypes.c_size_t, [_I32, _I32, _I64]),
     "pip_penalty_forward": (_INT, [_P, _I32, _P, _I32, _P, _I64, ctypes.c_float, _P, _P,
                                     ctypes.c_size_t, _P]),
@@ -253,6 +257,27 @@ def pip_autotune_stream(tables: Tables, points: torch.Tensor, mask: torch.Tensor
                                      points.numel() // 2, mask.data_ptr(), int(reps),
                                      _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
            "pip_autotune_stream")
+    return int(best.value), float(ms.value)
+
+
+def pip_batch_variant_count() -> int:
+    return int(lib().pip_batch_variant_count())
+
+
+def pip_set_batch_variant(tables: Tables, variant: int):
+    _check(lib().pip_set_batch_variant(tables, int(variant)), "pip_set_batch_variant")
+
+
+def pip_autotune_batch(tables: Tables, points: torch.Tensor, point_offsets: torch.Tensor,
+                       mask: torch.Tensor, reps: int = 3, stream=None) -> tuple[int, float]:
+    """Times every tile shape of the pipelined batch kernel on this batch; keeps the fastest."""
+    _dev(points, "points")
+    _dev(point_offsets, "point_offsets")
+    best = ctypes.c_int32(-1)
+    ms = ctypes.c_float(0.0)
+    _check(lib().pip_autotune_batch(tables, points.data_ptr(), _dtype_code(points), points.numel() // 2,
+                                    point_offsets.data_ptr(), mask.data_ptr(), int(reps), _stream(stream),
+                                    ctypes.byref(best), ctypes.byref(ms)), "pip_autotune_batch")
     return int(best.value), float(ms.value)
 
 

@@ -102,6 +102,7 @@ struct pip_tables {
     int32_t *d_error;            // runtime error of a kernel (PIP_E_TIMEOUT), sticky until read
     void *d_stream_ctr;          // counters of the pipelined kernel (zero between launches)
     int stream_variant;          // tile shape of the pipelined single-polygon kernel
+    int batch_variant;           // tile shape of the pipelined own-polygon batch kernel
     // one-polygon tables: a host copy of the polygon's row and coefficients,
     // passed to the pipelined kernel by value (constant bank, no registers)
     int have_host_poly;

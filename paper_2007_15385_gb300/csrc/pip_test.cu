@@ -56,20 +56,24 @@ cudaError_t launch_ragged(const pip_tables *t, const void *pts, int64_t M, const
 }
 
 // The pipelined own-polygon batch: setup (items, shared mask words, counters)
-// then the persistent kernel; 12 points a lane, three stages.
-constexpr int kRaggedPPL = 12;
-constexpr int kRaggedStages = 3;
+// then the persistent kernel.  Variants: (points per lane, ring stages); the
+// item tile is 8 warps x 32 lanes x points per lane.
+struct BatchVariant {
+    int ppl, stages;
+};
+constexpr BatchVariant kBatchVariants[] = {{12, 3}, {12, 4}, {8, 4}, {8, 6}};
+constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-template <bool INT>
-cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
-                              uint32_t *mask, cudaStream_t s)
+template <int PPL, int STAGES, bool INT>
+cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
+                                  uint32_t *mask, cudaStream_t s)
 {
-    using C = RaggedCfg<kRaggedPPL, kRaggedStages>;
+    using C = RaggedCfg<PPL, STAGES>;
     ragged_items_kernel<<<1, 1024, 0, s>>>(poffs, t->P, M, C::kTile, t->d_items, (RaggedItem *)t->d_ritems,
                                            t->ritems_cap, t->d_work, t->d_qcount, t->d_worst, mask);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    auto k = ragged_tma_kernel<kRaggedPPL, kRaggedStages, INT>;
+    auto k = ragged_tma_kernel<PPL, STAGES, INT>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRaggedThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
@@ -80,6 +84,30 @@ cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, c
                                                             t->d_work, mask, t->d_queue, t->d_keys, t->d_qcount,
                                                             t->d_error);
     return cudaGetLastError();
+}
+
+template <bool INT>
+cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
+                              uint32_t *mask, cudaStream_t s)
+{
+    switch (t->batch_variant) {
+    case 1: return launch_ragged_tma_one<12, 4, INT>(t, pts, M, poffs, mask, s);
+    case 2: return launch_ragged_tma_one<8, 4, INT>(t, pts, M, poffs, mask, s);
+    case 3: return launch_ragged_tma_one<8, 6, INT>(t, pts, M, poffs, mask, s);
+    default: return launch_ragged_tma_one<12, 3, INT>(t, pts, M, poffs, mask, s);
+    }
+}
+
+template <int PPL, int STAGES>
+cudaError_t set_ragged_attr()
+{
+    const int bytes = (int)RaggedCfg<PPL, STAGES>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -453,12 +481,10 @@ int stream_variant_count() { return kNumStreamVariants; }
 
 cudaError_t ragged_kernels_setup()
 {
-    const int bytes = (int)RaggedCfg<kRaggedPPL, kRaggedStages>::kSmem;
-    cudaError_t e = cudaFuncSetAttribute(ragged_tma_kernel<kRaggedPPL, kRaggedStages, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ragged_tma_kernel<kRaggedPPL, kRaggedStages, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = set_ragged_attr<12, 3>();
+    if (e == cudaSuccess) e = set_ragged_attr<12, 4>();
+    if (e == cudaSuccess) e = set_ragged_attr<8, 4>();
+    if (e == cudaSuccess) e = set_ragged_attr<8, 6>();
     return e;
 }
 
@@ -586,6 +612,64 @@ extern "C" pip_status pip_set_stream_variant(pip_tables *t, int32_t variant)
     if (st != PIP_OK) return st;
     if (variant < 0 || variant >= kNumStreamVariants) return PIP_E_INVALID_ARG;
     t->stream_variant = variant;
+    return PIP_OK;
+}
+
+extern "C" int32_t pip_batch_variant_count(void) { return kNumBatchVariants; }
+
+extern "C" pip_status pip_set_batch_variant(pip_tables *t, int32_t variant)
+{
+    pip_status st = check_tables(t);
+    if (st != PIP_OK) return st;
+    if (variant < 0 || variant >= kNumBatchVariants) return PIP_E_INVALID_ARG;
+    t->batch_variant = variant;
+    return PIP_OK;
+}
+
+extern "C" pip_status pip_autotune_batch(pip_tables *t, const void *d_points, pip_dtype pdtype,
+                                         int64_t num_points, const int64_t *d_point_offsets, uint32_t *d_mask,
+                                         int32_t reps, void *stream, int32_t *best_variant, float *best_ms)
+{
+    pip_status st = check_tables(t);
+    if (st != PIP_OK) return st;
+    if (num_points <= 0 || reps < 1 || d_point_offsets == nullptr || !aligned(d_points, 16))
+        return PIP_E_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    PIP_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return PIP_E_CUDA;
+    }
+    const int keep = t->timing;
+    t->timing = 0;
+    int best = -1;
+    float best_t = 0.f;
+    pip_status out = PIP_OK;
+    for (int v = 0; v < kNumBatchVariants && out == PIP_OK; ++v) {
+        t->batch_variant = v;
+        out = pip_test(t, d_points, pdtype, num_points, d_point_offsets, PIP_MASK, d_mask, nullptr, stream);
+        if (out != PIP_OK) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { out = PIP_E_CUDA; break; }
+        for (int r = 0; r < reps && out == PIP_OK; ++r)
+            out = pip_test(t, d_points, pdtype, num_points, d_point_offsets, PIP_MASK, d_mask, nullptr, stream);
+        if (out != PIP_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            out = PIP_E_CUDA;
+            break;
+        }
+        ms /= reps;
+        if (best < 0 || ms < best_t) { best = v; best_t = ms; }
+    }
+    t->timing = keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out != PIP_OK) return out;
+    t->batch_variant = best;
+    if (best_variant) *best_variant = best;
+    if (best_ms) *best_ms = best_t;
     return PIP_OK;
 }
 

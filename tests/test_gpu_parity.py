@@ -141,6 +141,31 @@ def test_gis_batch_unaligned_points():
     assert_same(got, oracle_own(w), "gis unaligned")
 
 
+@pytest.mark.parametrize("ints", [False, True])
+def test_every_batch_variant_matches_the_oracle_and_autotune_picks_one(ints):
+    w = (wl.integer_hulls(seed=20, num_polygons=24, points_per_polygon=2000) if ints
+         else wl.gis_batch(seed=21, num_polygons=40, m_range=(0, 9000)))
+    want = oracle_own(w)
+    dev_ = dev()
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev_), torch.from_numpy(w.vertex_offsets).to(dev_),
+                      max_points=w.num_points)
+    p = torch.from_numpy(w.points).to(dev_)
+    po = torch.from_numpy(w.point_offsets).to(dev_)
+    mbuf, mask = guarded((w.num_points + 31) // 32)
+    for v in range(B.pip_batch_variant_count()):
+        B.pip_set_batch_variant(t, v)
+        mask.fill_(-1)
+        B.pip_test(t, p, po, mask=mask)
+        st, _ = B.pip_get_status(t)
+        assert st == B.PIP_OK
+        check_guards(mbuf)
+        got = np.unpackbits(mask.cpu().numpy().view(np.uint8), bitorder="little")[:w.num_points]
+        assert_same(got, want, "batch variant %d" % v)
+    best, ms = B.pip_autotune_batch(t, p, po, mask, reps=2)
+    assert 0 <= best < B.pip_batch_variant_count() and ms > 0
+    t.close()
+
+
 def test_ragged_invalid_polygons_hold_nothing():
     sq = [[0, 0], [4, 0], [4, 4], [0, 4]]
     polys = [sq, [[0, 0], [2, 0], [1, 0.2], [2, 2], [0, 2]], [[0, 0], [1, 0], [2, 0]], sq,
