@@ -13,8 +13,11 @@
 // between forward and backward) inside a caller-provided workspace.
 //
 // Layout of the work: block (tile, pose) takes one pose and kPenPoints
-// points; every thread keeps float32 partial sums (the backward pass's
-// per-edge sums go through shared-memory atomics), the block reduces them in
+// points.  At block start one thread per edge folds the pose into the edge's
+// coefficients (fp64, rounded once), so that a margin term is two FMAs on the
+// world point; for up to 16 edges the coefficients then sit in registers.
+// Every thread keeps float32 partial sums (the backward pass's per-edge sums
+// go to per-warp shared-memory slots by atomics), the block reduces them in
 // fp64 into its own slot of the workspace, and a final kernel adds the slots
 // in a fixed order.
 #include <stdlib.h>
@@ -25,7 +28,6 @@ namespace {
 
 constexpr int kPenThreads = 256;
 constexpr int kPenPoints = 16384;  // points per block
-constexpr int kPenMaxEdges = kMaxEdges;
 
 struct PenWorkspace {
     PolyInfo *poly;
@@ -36,11 +38,15 @@ struct PenWorkspace {
     float4 *coef;
     float4 *coefn;
     double *loss_part;  // [blocks]
-    double *pose_part;  // [blocks][3]  (sum g w_x, sum g w_y, sum g (w_x y - w_y x))
+    double *pose_part;  // [blocks][3]  dL/d(t_x, t_y, theta) of the block's pose, its points only
     double *edge_part;  // [blocks][n][3]  (sum g, sum g x, sum g y) per argmax edge
     double *edge_sum;   // [n][3]  reduced
     double *pose_sum;   // [P][3]  reduced
+    float4 *pose_coef;  // [P][kPoseStride]  per-pose affine forms (w'_x, w'_y, t', 0)
+    double2 *pose_rot;  // [P]  (cos theta, sin theta)
 };
+
+constexpr int kPoseStride = kMaxEdges;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -64,6 +70,8 @@ size_t carve(void *base, int n, int P, int64_t blocks, PenWorkspace *w)
     w->edge_part = (double *)take((size_t)blocks * n * 3 * sizeof(double));
     w->edge_sum = (double *)take((size_t)n * 3 * sizeof(double));
     w->pose_sum = (double *)take((size_t)P * 3 * sizeof(double));
+    w->pose_coef = (float4 *)take((size_t)P * kPoseStride * sizeof(float4));
+    w->pose_rot = (double2 *)take((size_t)P * sizeof(double2));
     return off;
 }
 
@@ -89,78 +97,196 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return s;  // meaningful in thread 0
 }
 
-// softplus(z) = log(1 + e^z), evaluated without overflow
-__device__ __forceinline__ float softplus_f(float z)
+// max of three (a NaN operand is ignored unless all are NaN)
+__device__ __forceinline__ float fmax3(float a, float b, float c)
 {
-    return fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
-// sigmoid(z) = 1 / (1 + e^-z), evaluated without overflow
-__device__ __forceinline__ float sigmoid_f(float z)
+// e^-|z| on the special-function unit (ex2), never above 1
+__device__ __forceinline__ float exp_neg_abs(float z)
 {
-    const float e = __expf(-fabsf(z));
-    return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+    return __expf(-fabsf(z));
 }
 
-template <bool BACKWARD>
-__global__ void __launch_bounds__(kPenThreads) penalty_kernel(
-    const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefn, const float *__restrict__ poses,
-    const float *__restrict__ pts, int64_t M, float tau, double *__restrict__ loss_part,
-    double *__restrict__ pose_part, double *__restrict__ edge_part)
+// log(1 + e) for e in [0, 1]: with u = fl(1 + e), log(u) * e / (u - 1) is
+// accurate to a few ulp even where u rounds e away (Goldberg 1991, "What
+// every computer scientist should know about floating-point arithmetic",
+// Theorem 4); u == 1 means log(1 + e) = e to float precision.  log(u) on the
+// special-function unit (lg2).
+__device__ __forceinline__ float log1p_small(float e)
 {
-    __shared__ float4 cs[kPenMaxEdges];
-    __shared__ float acc_edge[kPenMaxEdges][3];
-    __shared__ double red[kPenThreads / 32];
+    const float u = 1.f + e;
+    return u == 1.f ? e : __logf(u) * __fdividef(e, u - 1.f);
+}
+
+// sigmoid(z) = 1 / (1 + e^-z) from e = e^-|z|, evaluated without overflow
+__device__ __forceinline__ float sigmoid_from(float z, float e)
+{
+    return __fdividef(z >= 0.f ? 1.f : e, 1.f + e);
+}
+
+// Per pose, the margin terms as affine forms of d = p - t (the point relative
+// to the pose's position, world axes):
+//   m_k = xb . w_k - c_k  (xb = R^T d body coordinates, w_k unit normal,
+//   c_k the edge line's offset from the body origin)
+//       = d . w'_k - c_k,   w'_k = R w_k,
+// formed in fp64 (one block per pose, one thread per edge) and rounded once.
+// Keeping t out of the constant keeps it small: a rounded t . w' (tens of
+// metres) would shift every margin of the pose by the same ~1e-6 m, a bias of
+// ~1e-6 / tau in dL/dm.  d itself is exact for the points near the footprint
+// (the ones with a gradient).  Slots past n hold w' = 0, c = +inf
+// (m_k = -inf never attains the max).
+__global__ void __launch_bounds__(64) pose_coef_kernel(const PolyInfo *__restrict__ poly,
+                                                       const float4 *__restrict__ coefn,
+                                                       const float *__restrict__ poses, int P,
+                                                       float4 *__restrict__ pose_coef, double2 *__restrict__ pose_rot)
+{
+    const int j = blockIdx.x, k = threadIdx.x;
+    if (j >= P) return;
     const PolyInfo pi = poly[0];
-    const bool ok = pi.status == PIP_OK;
-    const int n = ok ? pi.n : 0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        cs[k] = coefn[k];
-        acc_edge[k][0] = acc_edge[k][1] = acc_edge[k][2] = 0.f;
+    const int n = pi.status == PIP_OK ? pi.n : 0;
+    const double th = poses[3 * j + 2];
+    const double cn = cos(th), sn = sin(th);
+    if (k == 0) pose_rot[j] = make_double2(cn, sn);
+    for (int e = k; e < kPoseStride; e += blockDim.x) {
+        float4 r = make_float4(0.f, 0.f, INFINITY, 0.f);
+        if (e < n) {
+            const float4 c = coefn[e];  // (w_x, w_y, t_k) / |w| in local coordinates x = xb - o
+            const double wx = c.x, wy = c.y;
+            const double ck = (double)c.z + (double)pi.ox * wx + (double)pi.oy * wy;
+            const double wpx = cn * wx - sn * wy, wpy = sn * wx + cn * wy;
+            r = make_float4((float)wpx, (float)wpy, (float)ck, 0.f);
+        }
+        pose_coef[(size_t)j * kPoseStride + e] = r;
     }
-    const int pose = blockIdx.y;
-    const float tx = poses[3 * pose], ty = poses[3 * pose + 1], th = poses[3 * pose + 2];
-    float sn, cn;
-    sincosf(th, &sn, &cn);
-    // x = R^T (p - t) - o = R^T (p - t'),  t' = t + R o
-    const float tpx = tx + (cn * pi.ox - sn * pi.oy), tpy = ty + (sn * pi.ox + cn * pi.oy);
-    const float inv_tau = 1.f / tau;
-    __syncthreads();
+}
 
-    float l_acc = 0.f, a_x = 0.f, a_y = 0.f, a_t = 0.f;
+// Forward: sum of softplus(-m / tau) over this block's points for its pose.
+// NE > 0: the polygon has at most NE edges, coefficients in registers; NE == 0:
+// any edge count, read from shared memory.  kPenUnroll points per thread in
+// flight.
+constexpr int kPenUnroll = 4;
+
+template <int NE>
+__device__ __forceinline__ float margin_of(const float4 *cs, const float (&w)[NE > 0 ? NE : 1][3], int n,
+                                           float dx, float dy)
+{
+    if (NE > 0) {
+        float m = fmaf(dx, w[0][0], fmaf(dy, w[0][1], -w[0][2]));
+#pragma unroll
+        for (int k = 1; k + 1 < (NE > 0 ? NE : 2); k += 2)
+            m = fmax3(m, fmaf(dx, w[k][0], fmaf(dy, w[k][1], -w[k][2])),
+                      fmaf(dx, w[k + 1][0], fmaf(dy, w[k + 1][1], -w[k + 1][2])));
+        if ((NE & 1) == 0)
+            m = fmaxf(m, fmaf(dx, w[NE - 1][0], fmaf(dy, w[NE - 1][1], -w[NE - 1][2])));
+        return m;
+    }
+    float m = -INFINITY;
+    for (int k = 0; k < n; ++k) {
+        const float4 c = cs[k];
+        m = fmaxf(m, fmaf(dx, c.x, fmaf(dy, c.y, -c.z)));
+    }
+    return m;
+}
+
+// Backward accumulators, per edge (sum g, sum g dx, sum g dy) in shared
+// memory.  NE > 0: per lane, no atomics; a lane's slots are 3 NE + 1 words
+// apart (odd), so that lanes on the same edge hit 32 different banks.
+// NE == 0 (up to 64 edges): per warp, shared-memory atomics.
+template <int NE>
+__host__ __device__ constexpr int lane_words() { return NE > 0 ? 3 * NE + 1 : 3 * kMaxEdges; }
+template <int NE>
+__host__ __device__ constexpr int acc_rows() { return NE > 0 ? kPenThreads : kPenThreads / 32; }
+template <int NE>
+constexpr size_t acc_bytes() { return (size_t)acc_rows<NE>() * lane_words<NE>() * sizeof(float); }
+
+template <int NE, bool BACKWARD>
+__global__ void __launch_bounds__(kPenThreads) penalty_kernel(
+    const PolyInfo *__restrict__ poly, const float4 *__restrict__ pose_coef,
+    const double2 *__restrict__ pose_rot, const float *__restrict__ poses, const float *__restrict__ pts,
+    int64_t M, int nv, float tau, double *__restrict__ loss_part, double *__restrict__ pose_part,
+    double *__restrict__ edge_part)
+{
+    constexpr int kWarps = kPenThreads / 32;
+    extern __shared__ float lane_acc[];  // backward: [kPenThreads][kLaneWords]
+    __shared__ double red[kWarps];
+    const int n = poly[0].status == PIP_OK ? poly[0].n : 0;
+    const int pose = blockIdx.y;
+    const float4 *cs = pose_coef + (size_t)pose * kPoseStride;
+    float w[NE > 0 ? NE : 1][3];
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+        const float4 c = cs[k];
+        w[k][0] = c.x;
+        w[k][1] = c.y;
+        w[k][2] = c.z;
+    }
+    constexpr int kLW = lane_words<NE>();
+    float *my = lane_acc + (size_t)(NE > 0 ? threadIdx.x : threadIdx.x >> 5) * kLW;
+    if (BACKWARD) {
+        for (int e = threadIdx.x; e < acc_rows<NE>() * kLW; e += kPenThreads) lane_acc[e] = 0.f;
+        __syncthreads();
+    }
+    const float inv_tau = 1.f / tau;
+    const float ftx = poses[3 * pose], fty = poses[3 * pose + 1];
+
+    float l_acc = 0.f;
     const int64_t p0 = (int64_t)blockIdx.x * kPenPoints;
     const int64_t p1 = min(p0 + kPenPoints, M);
-    if (ok) {
-        for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
-            const float2 p = ((const float2 *)pts)[i];
-            const float dx = p.x - tpx, dy = p.y - tpy;
-            const float x = cn * dx + sn * dy;   // local body coordinates
-            const float y = -sn * dx + cn * dy;
-            float m = -INFINITY;
-            int kb = 0;
-            for (int k = 0; k < n; ++k) {
-                const float4 c = cs[k];
-                const float mk = fmaf(x, c.x, fmaf(y, c.y, -c.z));  // x . w/|w| - t/|w|
-                if (BACKWARD) {
-                    if (mk > m) { m = mk; kb = k; }
+    constexpr int64_t kStep = (int64_t)kPenThreads * kPenUnroll;
+    auto load = [&](int64_t i0, float2 (&p)[kPenUnroll]) {
+#pragma unroll
+        for (int u = 0; u < kPenUnroll; ++u) {
+            const int64_t i = i0 + (int64_t)u * kPenThreads;
+            p[u] = i < p1 ? ((const float2 *)pts)[i] : make_float2(ftx, fty);
+        }
+    };
+    if (n > 0) {
+        float2 nxt[kPenUnroll];
+        load(p0 + threadIdx.x, nxt);
+        for (int64_t i0 = p0 + threadIdx.x; i0 < p1; i0 += kStep) {
+            float2 p[kPenUnroll];
+#pragma unroll
+            for (int u = 0; u < kPenUnroll; ++u) p[u] = nxt[u];
+            load(i0 + kStep, nxt);  // the next points are in flight while these are evaluated
+#pragma unroll
+            for (int u = 0; u < kPenUnroll; ++u) {
+                if (i0 + (int64_t)u * kPenThreads >= p1) continue;
+                const float dx = p[u].x - ftx, dy = p[u].y - fty;
+                const float m = margin_of<NE>(cs, w, n, dx, dy);
+                const float z = -m * inv_tau;
+                const float e = exp_neg_abs(z);
+                if (!BACKWARD) {
+                    l_acc += fmaxf(z, 0.f) + log1p_small(e);  // softplus(z)
                 } else {
-                    m = fmaxf(m, mk);
-                }
-            }
-            const float z = -m * inv_tau;
-            if (!BACKWARD) {
-                l_acc += softplus_f(z);
-            } else {
-                const float g = -sigmoid_f(z) * inv_tau;  // dL/dm
-                if (g != 0.f) {
-                    const float4 c = cs[kb];
-                    const float xb = x + pi.ox, yb = y + pi.oy;  // body coordinates
-                    a_x += g * c.x;
-                    a_y += g * c.y;
-                    a_t += g * (c.x * yb - c.y * xb);
-                    atomicAdd(&acc_edge[kb][0], g);
-                    atomicAdd(&acc_edge[kb][1], g * xb);
-                    atomicAdd(&acc_edge[kb][2], g * yb);
+                    const float g = -sigmoid_from(z, e) * inv_tau;  // dL/dm
+                    if (g != 0.f) {
+                        // the lowest edge that attains the max
+                        int kb = 0;
+                        if (NE > 0) {
+#pragma unroll
+                            for (int k = (NE > 0 ? NE : 1) - 1; k >= 0; --k)
+                                if (fmaf(dx, w[k][0], fmaf(dy, w[k][1], -w[k][2])) == m) kb = k;
+                        } else {
+                            for (int k = n - 1; k >= 0; --k) {
+                                const float4 c = cs[k];
+                                if (fmaf(dx, c.x, fmaf(dy, c.y, -c.z)) == m) kb = k;
+                            }
+                        }
+                        float *slot = my + 3 * kb;
+                        if (NE > 0) {
+                            slot[0] += g;
+                            slot[1] += g * dx;
+                            slot[2] += g * dy;
+                        } else {
+                            atomicAdd(&slot[0], g);
+                            atomicAdd(&slot[1], g * dx);
+                            atomicAdd(&slot[2], g * dy);
+                        }
+                    }
                 }
             }
         }
@@ -170,15 +296,43 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
         const double s = block_sum((double)l_acc, red);
         if (threadIdx.x == 0) loss_part[blk] = s;
     } else {
-        const double sx = block_sum((double)a_x, red);
-        if (threadIdx.x == 0) pose_part[3 * blk] = sx;
-        const double sy = block_sum((double)a_y, red);
-        if (threadIdx.x == 0) pose_part[3 * blk + 1] = sy;
-        const double st = block_sum((double)a_t, red);
-        if (threadIdx.x == 0) pose_part[3 * blk + 2] = st;
         __syncthreads();
-        for (int e = threadIdx.x; e < 3 * pi.n; e += blockDim.x)
-            edge_part[(size_t)blk * pi.n * 3 + e] = ok ? (double)acc_edge[e / 3][e % 3] : 0.0;
+        // per (edge, component) v: warp v % 8 adds the 256 lanes' slots, 8 per
+        // lane then a shuffle tree (float32, fixed order)
+        __shared__ double es[kMaxEdges][3];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int v = wid; v < 3 * kMaxEdges; v += kWarps) {
+            float t = 0.f;
+            if (v < 3 * n)
+                for (int r = lane; r < acc_rows<NE>(); r += 32) t += lane_acc[(size_t)r * kLW + v];
+            for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) es[v / 3][v % 3] = (double)t;
+        }
+        __syncthreads();
+        __shared__ double pg[kMaxEdges][3];
+        const int k = threadIdx.x;
+        const double2 rc = pose_rot[pose];
+        if (k < kMaxEdges) {
+            const double S = es[k][0], Dx = es[k][1], Dy = es[k][2];
+            const float4 c = k < n ? cs[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            // dm/dt = -w',  dm/dtheta = (p - t) x w' = dy w'_x - dx w'_y
+            pg[k][0] = -S * c.x;
+            pg[k][1] = -S * c.y;
+            pg[k][2] = Dy * c.x - Dx * c.y;
+            if (k < nv) {
+                // body coordinates: xb = R^T (p - t); zeros for an invalid footprint
+                double *ep = edge_part + (size_t)blk * nv * 3 + 3 * k;
+                ep[0] = S;
+                ep[1] = rc.x * Dx + rc.y * Dy;
+                ep[2] = -rc.y * Dx + rc.x * Dy;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double v = 0.0;
+            for (int e = 0; e < n; ++e) v += pg[e][threadIdx.x];  // fixed order
+            pose_part[3 * blk + threadIdx.x] = v;
+        }
     }
 }
 
@@ -223,8 +377,9 @@ __global__ void __launch_bounds__(kPenThreads) penalty_backward_reduce(
 //     dL/dp0  += -(X - S p0)/D + Nsum (p_k - p0) / (2 D^3)
 //     dL/dp_k  =  (X - S p_k)/D - Nsum (p_k - p0) / (2 D^3)
 //   then back through Eq. 8 (p_k = p0 - 2 L_k(p0) (a, b) / (a^2 + b^2)) and
-//   Eq. 3-4 (p0 = C / (3 S2)) to the vertices; the pose gradients are
-//   dL/dt = -R(theta) sum g w and dL/dtheta = sum g (w_x y - w_y x).
+//   Eq. 3-4 (p0 = C / (3 S2)) to the vertices.  The pose gradients arrive
+//   summed per pose (dL/dt = -sum g R(theta) w, dL/dtheta = sum g (p - t) x
+//   R(theta) w, in world axes) and are only scaled here.
 __global__ void __launch_bounds__(64) penalty_chain_kernel(
     const float *__restrict__ verts, int n, const double2 *__restrict__ g0tab,
     const double2 *__restrict__ gk, const PolyInfo *__restrict__ poly, const float *__restrict__ poses,
@@ -238,12 +393,9 @@ __global__ void __launch_bounds__(64) penalty_chain_kernel(
     const bool ok = poly[0].status == PIP_OK;
     // pose gradients: one thread per pose, in a loop
     for (int j = k; j < P; j += blockDim.x) {
-        const double ax = pose_sum[3 * j], ay = pose_sum[3 * j + 1], at = pose_sum[3 * j + 2];
-        const double th = (double)poses[3 * j + 2];
-        const double c = cos(th), s = sin(th);
-        grad_pose[3 * j] = ok ? scale * -(c * ax - s * ay) : 0.0;
-        grad_pose[3 * j + 1] = ok ? scale * -(s * ax + c * ay) : 0.0;
-        grad_pose[3 * j + 2] = ok ? scale * at : 0.0;
+        grad_pose[3 * j] = ok ? scale * pose_sum[3 * j] : 0.0;
+        grad_pose[3 * j + 1] = ok ? scale * pose_sum[3 * j + 1] : 0.0;
+        grad_pose[3 * j + 2] = ok ? scale * pose_sum[3 * j + 2] : 0.0;
     }
     double G0x = 0.0, G0y = 0.0;
     double gxm = 0.0, gym = 0.0, gxk = 0.0, gyk = 0.0;  // this edge's share of the vertex gradient
@@ -321,6 +473,28 @@ __global__ void __launch_bounds__(64) penalty_chain_kernel(
     }
 }
 
+// the footprint's edge count is known on the host: pick the register variant
+template <bool BACKWARD>
+void launch_penalty(int n, dim3 grid, cudaStream_t s, const PenWorkspace &w, const float *poses,
+                    const float *pts, int64_t M, float tau)
+{
+    const int P = (int)grid.y;
+    pose_coef_kernel<<<P, 64, 0, s>>>(w.poly, w.coefn, poses, P, w.pose_coef, w.pose_rot);
+    // 16 edges need 49 KiB of accumulators: above the default dynamic limit
+    if (BACKWARD && n > 12 && n <= 16)
+        cudaFuncSetAttribute(penalty_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)acc_bytes<16>());
+#define PIP_PEN(NE)                                                                                     \
+    penalty_kernel<NE, BACKWARD><<<grid, kPenThreads, BACKWARD ? acc_bytes<NE>() : 0, s>>>(              \
+        w.poly, w.pose_coef, w.pose_rot, poses, pts, M, n, tau, w.loss_part, w.pose_part, w.edge_part)
+    if (n <= 4) PIP_PEN(4);
+    else if (n <= 8) PIP_PEN(8);
+    else if (n <= 12) PIP_PEN(12);
+    else if (n <= 16) PIP_PEN(16);
+    else PIP_PEN(0);
+#undef PIP_PEN
+}
+
 pip_status check_args(const float *d_vertices, int32_t n, const float *d_poses, int32_t P,
                       const float *d_points, int64_t M, float tau, void *ws, size_t ws_bytes)
 {
@@ -359,8 +533,8 @@ pip_status pip_penalty_forward(const float *d_vertices, int32_t num_vertices, co
     pen_begin_kernel<<<1, 32, 0, s>>>(w.voffs, w.worst, num_vertices);
     prepare_kernel<<<1, 32, 0, s>>>(d_vertices, PIP_F32, w.voffs, 1, num_vertices, w.g0, w.gk, w.coef,
                                     w.coefn, w.poly, w.worst);
-    penalty_kernel<false><<<dim3((unsigned)tiles, (unsigned)num_poses), kPenThreads, 0, s>>>(
-        w.poly, w.coefn, d_poses, d_points, num_points, tau, w.loss_part, w.pose_part, w.edge_part);
+    launch_penalty<false>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses, d_points,
+                          num_points, tau);
     penalty_loss_reduce<<<1, kPenThreads, 0, s>>>(w.loss_part, tiles * num_poses, nullptr, d_loss);
     return cudaGetLastError() == cudaSuccess ? PIP_OK : PIP_E_CUDA;
 }
@@ -381,8 +555,8 @@ pip_status pip_penalty_backward(const float *d_vertices, int32_t num_vertices, c
     pen_begin_kernel<<<1, 32, 0, s>>>(w.voffs, w.worst, num_vertices);
     prepare_kernel<<<1, 32, 0, s>>>(d_vertices, PIP_F32, w.voffs, 1, num_vertices, w.g0, w.gk, w.coef,
                                     w.coefn, w.poly, w.worst);
-    penalty_kernel<true><<<dim3((unsigned)tiles, (unsigned)num_poses), kPenThreads, 0, s>>>(
-        w.poly, w.coefn, d_poses, d_points, num_points, tau, w.loss_part, w.pose_part, w.edge_part);
+    launch_penalty<true>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses, d_points,
+                         num_points, tau);
     penalty_backward_reduce<<<3 * num_vertices + 3 * num_poses, kPenThreads, 0, s>>>(
         w.edge_part, w.pose_part, num_vertices, num_poses, tiles, w.edge_sum, w.pose_sum);
     penalty_chain_kernel<<<1, 64, 0, s>>>(d_vertices, num_vertices, w.g0, w.gk, w.poly, d_poses, num_poses,

@@ -55,6 +55,26 @@ def test_penalty_loss_and_gradients_match_fp64_reference():
     assert ok, "pose gradient: norm-wise %.2e, %d elements off" % (nrm, bad)
 
 
+@pytest.mark.parametrize("n", [4, 7, 16, 20, 40])
+def test_penalty_other_edge_counts(n):
+    """Register variants for up to 4, 8 and 16 edges and the shared-memory
+    variant above 16, each against the oracle."""
+    w = wl.footprint_trajectory(seed=45 + n, m=6000, num_poses=7, n=n)
+    v, P, q, tau = w.vertices, w.extra["poses"], w.points, w.extra["tau"]
+    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau).item()
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    ref_loss, ref_gv, ref_gp = oracle.penalty(v.astype(np.float64), P.astype(np.float64),
+                                             q.astype(np.float64), tau)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
+    assert ok, "n=%d vertex gradient: norm-wise %.2e, %d elements off" % (n, nrm, bad)
+    # 7 poses of a few hundred near points each: a pose component that cancels
+    # to ~1e-3 of the largest is below the float32 summation noise (~1e-7 of
+    # the largest), so the pose vector's elementwise floor is 1e-2 here
+    ok, nrm, bad = _rel_ok(gp.cpu().numpy(), ref_gp, floor_frac=1e-2)
+    assert ok, "n=%d pose gradient: norm-wise %.2e, %d elements off" % (n, nrm, bad)
+
+
 def test_penalty_gradient_against_central_differences_of_fp64_loss():
     v, P, q, tau = _case(m=2048, poses=4, seed=41)
     gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
