@@ -230,10 +230,12 @@ __global__ void __launch_bounds__(256) prepare_kernel(
     A = warp_max(A);
 
     if (lane == 0) {
-        // Error bound of the float32 test (derivation in the design notes):
+        // Error bound of the float32 test, |computed s_k - exact s_k| <= B:
         // FMA chain 2.01u(|t| + |w|_1 |x|_inf), point rounding u |w|_1 |x|_inf,
         // coefficient rounding u(|t| + |w|_1 |x|_inf), fp64 construction error
-        // E per coordinate of the generators; every constant doubled.
+        // E per coordinate of the generators; every constant doubled.  The
+        // kernels use B = beta0 + beta1 (|x| + |y|) or beta1 max(|x|, |y|),
+        // both at least beta0 + beta1 |x|_inf.
         const double u = ldexp(1.0, -24);
         const double E = ldexp(G + D, -40);
         const double b0 = 8.0 * u * tmax + 64.0 * E * (G + D) + ldexp(1.0, -120);
