@@ -212,7 +212,7 @@ def main():
                     help="points of the workload (default the full 2^26; smaller only for profiling)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "gis_batch", "gis_all_pairs", "integer_hulls",
-                             "footprint_trajectory", "unit_circle_octagon"],
+                             "footprint_trajectory", "unit_circle_octagon", "paper_sweep"],
                     help="which workload to time (the default is the headline)")
     ap.add_argument("--polygons", type=int, default=0,
                     help="number of polygons of the batch workloads (0: the workload's own; "
@@ -226,6 +226,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "paper_sweep":
+        return run_sweep(args)
     if args.workload != WORKLOAD:
         return run_other(args)
 
@@ -402,6 +404,58 @@ def time_steps(fn, steps: int, warmup: int, stream) -> float:
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps
+
+
+def run_sweep(args):
+    """The paper's experiment (Sec. 6.2) on the GPU: one convex polygon of n =
+    3..15 edges on the unit circle, random points around it, Voronoi against
+    sign of offset, ray crossing and the plain fp64 Voronoi form, in batches of
+    10^6 points (the paper's batch; L2-resident, launch-bound) and of 2^25
+    points (HBM-bound)."""
+    import torch
+
+    from paper_2007_15385_gb300 import binding as B
+    from paper_2007_15385_gb300 import workloads as wl
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    reps = max(3, args.steps)
+    sizes = {"batch_1e6": 10 ** 6, "stream_2e25": 1 << 25}
+    rows = {k: [] for k in sizes}
+    for n in range(3, 16):
+        big = wl.unit_circle_octagon(seed=100 + n, m=sizes["stream_2e25"], n=n)
+        v = torch.from_numpy(big.vertices).to(dev)
+        vo = torch.from_numpy(big.vertex_offsets).to(dev)
+        t = B.pip_prepare(v, vo, max_points=big.num_points)
+        p_all = torch.from_numpy(big.points).to(dev)
+        for key, m in sizes.items():
+            p = p_all[:m]
+            mask = torch.empty((m + 31) // 32, dtype=torch.int32, device=dev)
+            row = {"n": n}
+            for name, fn in (("voronoi", lambda: B.pip_test(t, p, mask=mask)),
+                             ("sign_of_offset", lambda: B.pip_test_sign_of_offset(t, p, mask=mask)),
+                             ("ray_crossing", lambda: B.pip_test_ray_crossing(t, p, mask=mask)),
+                             ("voronoi_plain_fp64", lambda: B.pip_test_voronoi_fp64(t, p, mask=mask))):
+                r = reps if name != "voronoi_plain_fp64" or key == "batch_1e6" else 3
+                ms = time_steps(fn, r, 3, stream)
+                row[name] = {"ms": ms, "Gtests_per_s": m * n / (ms * 1e-3) / 1e9}
+            rows[key].append(row)
+        t.close()
+    clk = clocks.stop()
+    vor = [r["voronoi"]["Gtests_per_s"] for r in rows["batch_1e6"]]
+    value = float(np.exp(np.mean(np.log(vor))))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": reps,
+            "warmup": 3, "ms_per_step": float(np.mean([r["voronoi"]["ms"] for r in rows["batch_1e6"]])),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "paper_sweep", "edges": "3..15", "polygon": "n sorted random angles on the unit circle",
+                       "points": "uniform in [-1.5, 1.5]^2", "value": "geometric mean over n of Voronoi Gtests/s, 10^6-point batches"},
+            "clocks": clk, "gpu_launches": 13 * 2 * 4 * (reps + 3), "sweep": rows}
+    print(json.dumps(line))
+    return 0
 
 
 def run_other(args):

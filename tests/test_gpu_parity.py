@@ -100,6 +100,16 @@ def test_octagon_full_size():
     assert_same(got, oracle_own(w), "octagon")
 
 
+@pytest.mark.parametrize("n", list(range(3, 16)))
+def test_paper_sweep_polygons(n):
+    """The polygons of the paper's edge-count sweep (n = 3..15, random angles on
+    the unit circle, points around it), as bench.py's paper_sweep times them."""
+    w = wl.unit_circle_octagon(seed=100 + n, m=60_001, n=n)
+    got, _, _, st = run_test(w)
+    assert st == B.PIP_OK
+    assert_same(got, oracle_own(w), "sweep n=%d" % n)
+
+
 @pytest.mark.parametrize("m", [1, 31, 33, 63, 64, 65, 257, 100_003])
 def test_vehicle_footprint_ragged_tails(m):
     w = wl.vehicle_footprint(m=m)
