@@ -533,6 +533,13 @@ def run_other(args):
         with torch.cuda.graph(graph):
             call()
         extra["graph_ms_per_step"] = time_steps(graph.replay, args.steps, 3, stream)
+        if args.workload == "gis_all_pairs":
+            # bounding-box cull and early stop (PIP_CULL): same results, less work;
+            # reported apart as an effective rate, not as the full-work value
+            cull = lambda: B.pip_test(t, p, po, mode=mode | B.PIP_CULL, mask=mask, first_hit=hit)
+            cms = time_steps(cull, args.steps, 3, stream)
+            extra["culled"] = {"ms_per_step": cms, "effective_Gtests_per_s": tests / (cms * 1e-3) / 1e9,
+                               "note": "PIP_CULL: polygons skipped per warp by bounding box, early stop"}
         launches = 3 if po is not None else (1 if (len(w.vertex_offsets) == 2 and p.data_ptr() % 16 == 0) else 2)
         t.close()
     clk = clocks.stop()

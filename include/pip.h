@@ -57,7 +57,7 @@ typedef enum {
 typedef enum { PIP_F32 = 0, PIP_I32 = 1 } pip_dtype;
 
 /* pip_test output selection (bit flags) */
-enum { PIP_MASK = 1, PIP_FIRST_HIT = 2 };
+enum { PIP_MASK = 1, PIP_FIRST_HIT = 2, PIP_CULL = 4 };
 
 /* Opaque: device tables built from a batch of polygons (generators,
  * coefficients, bounds, validation results) plus the refine workspace. */
@@ -106,7 +106,12 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype,
  *                     owns points [offs[j], offs[j+1]) (own-polygon batch),
  *                     offs[num_polygons] = num_points.
  *   mode              PIP_MASK and/or PIP_FIRST_HIT (first hit only when
- *                     d_point_offsets is NULL).
+ *                     d_point_offsets is NULL); PIP_CULL may be added for
+ *                     the all-pairs test: a polygon is skipped for a warp's
+ *                     points when none lies in its vertex bounding box, and
+ *                     a block stops once each of its points has a candidate.
+ *                     Same results, less work; not the paper's full-work
+ *                     timing convention (Sec. 6.2).  Ignored otherwise.
  *   d_mask            device uint32 [ceil(num_points / 32)]; bit (i % 32) of
  *                     word (i / 32) is 1 when point i is inside its polygon
  *                     (own-polygon batch) or inside at least one polygon

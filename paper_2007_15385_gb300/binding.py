@@ -28,6 +28,7 @@ PIP_F32 = 0
 PIP_I32 = 1
 PIP_MASK = 1
 PIP_FIRST_HIT = 2
+PIP_CULL = 4  # all pairs: skip polygons by bounding box, stop early (same results)
 
 # every symbol include/pip.h declares, with (restype, argtypes)
 _P = ctypes.c_void_p

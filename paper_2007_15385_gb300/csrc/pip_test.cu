@@ -138,7 +138,13 @@ __device__ __forceinline__ float ap_s(const float4 &c, float x, float y)
     return fmaf(-x, c.x, fmaf(-y, c.y, c.z));
 }
 
-template <bool INT>
+// CULL (pip_test's PIP_CULL): a warp skips a polygon when none of its points
+// that still lacks a candidate lies in the polygon's vertex bounding box (the
+// polygon lies inside that box exactly, and float32 rounding of a point is
+// monotone, so a skipped point is outside), and a CTA stops once every one of
+// its points has a candidate in its range (a later polygon cannot lower it).
+// Same keys for every point whose first hit lies in the range; fewer tests.
+template <bool INT, bool CULL>
 __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, int P, const void *__restrict__ pts,
     int64_t M, uint32_t *__restrict__ keys, int *__restrict__ err)
@@ -183,6 +189,7 @@ __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
         key[i] = (!INT || int_exact(px[i], py[i]) || jlo >= jhi) ? 0xffffffffu : ((uint32_t)jlo << 1) | 1u;
     }
     int c = 0;
+    bool early = false;  // CULL: stopped after consuming chunk c - 1
     for (; c < nchunks; ++c) {
         if (!mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), err)) break;
         const unsigned char *buf = smem + (size_t)(c & 1) * kApBufBytes;
@@ -193,6 +200,14 @@ __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
         for (int q = 0; q < nj; ++q) {
             const PolyInfo &pi = info[q];
             if (pi.status != PIP_OK) continue;  // an invalid polygon contains no point
+            if (CULL) {
+                const float bx0 = pi.bbox[0], by0 = pi.bbox[1], bx1 = pi.bbox[2], by1 = pi.bbox[3];
+                bool open = false;
+#pragma unroll
+                for (int i = 0; i < kApPT; ++i)
+                    open |= key[i] == 0xffffffffu && px[i] >= bx0 && px[i] <= bx1 && py[i] >= by0 && py[i] <= by1;
+                if (!__any_sync(0xffffffffu, open)) continue;
+            }
             const float ox = pi.ox, oy = pi.oy;
             const int n = pi.n;  // at least 3
             const float4 *cf = rows + q * kPadStride;
@@ -248,12 +263,26 @@ __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
                 }
             }
         }
-        __syncthreads();  // every warp is done with this buffer
+        if (CULL) {
+            // every warp is done with this buffer; stop when every point has a candidate
+            bool settled = true;
+#pragma unroll
+            for (int i = 0; i < kApPT; ++i) settled &= key[i] != 0xffffffffu || base + i * kApThreads + tid >= M;
+            if (__syncthreads_and(settled)) {
+                ++c;  // this chunk was consumed
+                early = true;
+                break;
+            }
+        } else {
+            __syncthreads();  // every warp is done with this buffer
+        }
         if (tid == 0 && c + 2 < nchunks) issue(c + 2);
     }
     if (c < nchunks && tid == 0) {
-        // gave up waiting: let the copies still in flight land before leaving
-        for (int k = c; k < nchunks && k < c + 2; ++k) mbar_wait(&full[k & 1], (uint32_t)((k >> 1) & 1), err);
+        // gave up waiting on chunk c (chunks c and c + 1 may be in flight), or
+        // stopped early with chunk c in flight: let those copies land first
+        const int end = min(nchunks, c + (early ? 1 : 2));
+        for (int k = c; k < end; ++k) mbar_wait(&full[k & 1], (uint32_t)((k >> 1) & 1), err);
     }
 #pragma unroll
     for (int i = 0; i < kApPT; ++i) {
@@ -287,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) allpairs_finalize_kernel(
     }
 }
 
-template <bool INT>
+template <bool INT, bool CULL>
 cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int32_t *first_hit,
                             uint32_t *mask, cudaStream_t s)
 {
@@ -295,7 +324,7 @@ cudaError_t launch_allpairs(const pip_tables *t, const void *pts, int64_t M, int
     if (e != cudaSuccess) return e;
     const int64_t tiles = (M + kApPT * kApThreads - 1) / (kApPT * kApThreads);
     const int split = t->P < kApSplit ? t->P : kApSplit;
-    allpairs_split_kernel<INT><<<dim3((unsigned)tiles, (unsigned)split), kApThreads, kApSmem, s>>>(
+    allpairs_split_kernel<INT, CULL><<<dim3((unsigned)tiles, (unsigned)split), kApThreads, kApSmem, s>>>(
         t->d_poly, t->d_coefp, t->P, pts, M, t->d_keys, t->d_error);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -490,11 +519,18 @@ cudaError_t ragged_kernels_setup()
 
 cudaError_t allpairs_setup()
 {
-    cudaError_t e = cudaFuncSetAttribute(allpairs_split_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApSmem);
+    const int bytes = (int)kApSmem;
+    cudaError_t e = cudaFuncSetAttribute(allpairs_split_kernel<false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(allpairs_split_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kApSmem);
+        e = cudaFuncSetAttribute(allpairs_split_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(allpairs_split_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(allpairs_split_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
     return e;
 }
 
@@ -509,7 +545,8 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     if (pdtype != PIP_F32 && pdtype != PIP_I32) return PIP_E_INVALID_ARG;
     if (num_points < 0) return PIP_E_INVALID_ARG;
     if (num_points > t->capacity) return PIP_E_CAPACITY;
-    if ((mode & ~(PIP_MASK | PIP_FIRST_HIT)) || mode == 0) return PIP_E_INVALID_ARG;
+    if ((mode & ~(PIP_MASK | PIP_FIRST_HIT | PIP_CULL)) || !(mode & (PIP_MASK | PIP_FIRST_HIT)))
+        return PIP_E_INVALID_ARG;
     const bool want_mask = mode & PIP_MASK, want_hit = mode & PIP_FIRST_HIT;
     if (want_hit && d_point_offsets != nullptr) return PIP_E_INVALID_ARG;
     if (num_points == 0) {  // nothing to decide; the refine count of this call is 0
@@ -568,8 +605,12 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
         PIP_CUDA_TRY(cudaMemsetAsync(t->d_qcount, 0, sizeof(unsigned int), s));
         if (num_points == 0) return PIP_OK;
         timing_mark(t, 0, s);
-        e = ints ? launch_allpairs<true>(t, d_points, num_points, hit, mask, s)
-                 : launch_allpairs<false>(t, d_points, num_points, hit, mask, s);
+        if (mode & PIP_CULL)
+            e = ints ? launch_allpairs<true, true>(t, d_points, num_points, hit, mask, s)
+                     : launch_allpairs<false, true>(t, d_points, num_points, hit, mask, s);
+        else
+            e = ints ? launch_allpairs<true, false>(t, d_points, num_points, hit, mask, s)
+                     : launch_allpairs<false, false>(t, d_points, num_points, hit, mask, s);
     }
     if (e != cudaSuccess) return PIP_E_CUDA;
     timing_mark(t, 1, s);

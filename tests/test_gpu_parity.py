@@ -217,6 +217,19 @@ def test_all_pairs_first_hit_small():
     assert_same(got, (want >= 0).astype(np.uint8), "all-pairs mask")
 
 
+@pytest.mark.parametrize("ints", [False, True])
+def test_all_pairs_culled_first_hit(ints):
+    if ints:
+        h = wl.integer_hulls(seed=31, num_polygons=40, points_per_polygon=700)
+        w = wl.Workload("int_all_pairs", h.vertices, h.vertex_offsets, h.points, None)
+    else:
+        w = wl.gis_all_pairs(seed=32, num_polygons=96, m=40_003, total_polygons=96)
+    got, fh, refine, st = run_test(w, mode=B.PIP_MASK | B.PIP_FIRST_HIT | B.PIP_CULL)
+    want = oracle.first_hit_exact(w.vertices, w.vertex_offsets, w.points)
+    assert_same(fh, want, "culled first hit")
+    assert_same(got, (want >= 0).astype(np.uint8), "culled mask")
+
+
 def test_all_pairs_mask_only():
     w = wl.gis_all_pairs(seed=15, num_polygons=40, m=5_000, total_polygons=40)
     got, _, _, _ = run_test(w, mode=B.PIP_MASK)
@@ -548,6 +561,14 @@ def test_all_pairs_full_size_sampled():
     idx = rng.choice(w.num_points, size=4000, replace=False)
     want = oracle.first_hit_exact(w.vertices, w.vertex_offsets, w.points[idx])
     assert_same(fh[idx], want, "all pairs sample")
+
+
+def test_all_pairs_culled_equals_full_work_at_full_size():
+    w = wl.gis_all_pairs()
+    got_f, fh_f, _, _ = run_test(w, mode=B.PIP_FIRST_HIT | B.PIP_MASK)
+    got_c, fh_c, _, _ = run_test(w, mode=B.PIP_FIRST_HIT | B.PIP_MASK | B.PIP_CULL)
+    assert_same(fh_c, fh_f, "culled vs full work, every point")
+    assert_same(got_c, got_f, "culled vs full work mask")
 
 
 def test_integer_hulls_full_size_sampled():
