@@ -212,7 +212,7 @@ def main():
                     help="points of the workload (default the full 2^26; smaller only for profiling)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "gis_batch", "gis_all_pairs", "integer_hulls",
-                             "footprint_trajectory", "unit_circle_octagon", "paper_sweep"],
+                             "footprint_trajectory", "unit_circle_octagon", "paper_sweep", "gis_raster"],
                     help="which workload to time (the default is the headline)")
     ap.add_argument("--polygons", type=int, default=0,
                     help="number of polygons of the batch workloads (0: the workload's own; "
@@ -228,6 +228,8 @@ def main():
         return run_reference(args)
     if args.workload == "paper_sweep":
         return run_sweep(args)
+    if args.workload == "gis_raster":
+        return run_raster(args)
     if args.workload != WORKLOAD:
         return run_other(args)
 
@@ -454,6 +456,53 @@ def run_sweep(args):
             "config": {"workload": "paper_sweep", "edges": "3..15", "polygon": "n sorted random angles on the unit circle",
                        "points": "uniform in [-1.5, 1.5]^2", "value": "geometric mean over n of Voronoi Gtests/s, 10^6-point batches"},
             "clocks": clk, "gpu_launches": 13 * 2 * 4 * (reps + 3), "sweep": rows}
+    print(json.dumps(line))
+    return 0
+
+
+def run_raster(args):
+    """Pixel coverage (pip_rasterize) of the 4,096 GIS polygons on a 3840 x 2160
+    frame spanning their [0, 10^4]^2 domain: first-hit id and mask per pixel."""
+    import torch
+
+    from paper_2007_15385_gb300 import binding as B
+    from paper_2007_15385_gb300 import workloads as wl
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    w = wl.gis_batch(num_polygons=args.polygons) if args.polygons > 0 else wl.gis_batch()
+    W, H = 3840, 2160
+    dx, dy = float(np.float32(1e4 / W)), float(np.float32(1e4 / H))
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev), torch.from_numpy(w.vertex_offsets).to(dev),
+                      max_points=W * H)
+    ids = torch.empty((H, W), dtype=torch.int32, device=dev)
+    mask = torch.empty((H, (W + 31) // 32), dtype=torch.int32, device=dev)
+    ws = torch.empty(B.pip_raster_workspace_bytes(t.num_polygons, W, H) + 16, dtype=torch.uint8, device=dev)
+    call = lambda: B.pip_rasterize(t, W, H, 0.0, 0.0, dx, dy, first_hit=ids, mask=mask, workspace=ws)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    ms = time_steps(call, args.steps, args.warmup, stream)
+    B.pip_timing(t, True)
+    for _ in range(args.steps):
+        call()
+    calls, bulk_ms, refine_ms = B.pip_timing_read(t)
+    B.pip_timing(t, False)
+    _, refined = B.pip_get_status(t)
+    clk = clocks.stop()
+    covered = int((ids >= 0).sum().item())
+    t.close()
+    px = W * H
+    line = {"metric": "pixels/s (pixel-centre coverage, first-hit id + mask)", "value": px / (ms * 1e-3) / 1e9,
+            "unit": "Gpixels/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "gis_raster", "width": W, "height": H, "num_polygons": w.num_polygons,
+                       "frame": "[0, 1e4]^2", "covered_pixels": covered},
+            "clocks": clk, "gpu_launches": 4 * args.steps,
+            "tile_and_finalize_ms": bulk_ms / max(1, calls), "refine_ms": refine_ms / max(1, calls),
+            "refined_pixels_per_step": refined,
+            "output_bytes_per_step": px * 4 + H * ((W + 31) // 32) * 4}
     print(json.dumps(line))
     return 0
 

@@ -318,6 +318,38 @@ pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype vdtype, int
                                    uint32_t *d_mask, int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------------
+ * pip_rasterize -- pixel coverage of the prepared polygons (the screen-space
+ * use of the inclusion test, Sec. 1: each pixel's membership decided by a
+ * point inclusion test at its centre).  Pixel (c, r), 0 <= c < width,
+ * 0 <= r < height, has the float32 centre
+ *     (fmaf((float)c, dx, x0), fmaf((float)r, dy, y0))
+ * (one rounding each); the results are those of pip_test's all-pairs test on
+ * those centres, bit-exact (closed polygons, fp64 / exact refine).
+ *
+ *   width, height   1 .. 2^24 each, width * height <= max_points of pip_prepare
+ *   x0, y0, dx, dy  finite, dx > 0, dy > 0, the last centre finite
+ *   d_first_hit     device int32 [height][width] (row-major) or NULL: the
+ *                   lowest polygon index whose closed polygon holds the
+ *                   pixel's centre (front to back), or -1
+ *   d_mask          device uint32 [height][ceil(width / 32)] or NULL (not
+ *                   both NULL): bit (c % 32) of word r * ceil(width / 32) +
+ *                   c / 32 is 1 when some polygon holds pixel (c, r); bits
+ *                   past width are 0
+ *   d_workspace     device, >= pip_raster_workspace_bytes(num_polygons,
+ *                   width, height) bytes (a tile x polygon bitmask),
+ *                   16-byte aligned, owned by the caller
+ *
+ * Shares the tables' refine queue and candidate keys with pip_test (calls on
+ * the same tables must not overlap).  No allocation, no host
+ * synchronisation; graph-capturable.  PIP_E_CAPACITY when width * height
+ * exceeds max_points, PIP_E_INVALID_ARG for a bad grid or buffer.
+ * ------------------------------------------------------------------------ */
+size_t pip_raster_workspace_bytes(int32_t num_polygons, int32_t width, int32_t height);
+pip_status pip_rasterize(const pip_tables *t, int32_t width, int32_t height, float x0, float y0, float dx,
+                         float dy, int32_t *d_first_hit, uint32_t *d_mask, void *d_workspace,
+                         size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * pip_selftest_wait_timeout -- the paper has no counterpart to this call; it
  * exercises the failure path that every pipelined kernel takes when one of
  * its waits never completes (a lost producer or consumer).

@@ -88,6 +88,8 @@ def _get():
             "orc_inside_exact": (i32, [P, i32, i32, P, i32, i64, P]),
             "orc_inside_exact_ragged": (i32, [P, i32, P, i32, P, i32, P, P]),
             "orc_first_hit_exact": (i32, [P, i32, P, i32, P, i32, i64, P]),
+            "orc_raster_centres": (None, [i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                          ctypes.c_float, P]),
             "orc_sign_of_offset": (None, [P, P, i32, P, i64, P]),
             "orc_ray_crossing": (None, [P, P, i32, P, i64, P]),
             "orc_margin": (i32, [P, P, i32, P, i64, P]),
@@ -200,6 +202,13 @@ def first_hit_exact(verts, voffs, pts):
     out = np.empty(m, np.int32)
     _get().orc_first_hit_exact(_ptr(verts), _dtype_code(verts), _ptr(voffs), len(voffs) - 1,
                                _ptr(pts), _dtype_code(pts), m, _ptr(out))
+    return out
+
+
+def raster_centres(width, height, x0, y0, dx, dy) -> np.ndarray:
+    """Pixel centres of the rasterisation grid, float32 [height * width, 2] row-major."""
+    out = np.empty((int(width) * int(height), 2), np.float32)
+    _get().orc_raster_centres(int(width), int(height), float(x0), float(y0), float(dx), float(dy), _ptr(out))
     return out
 
 

@@ -668,3 +668,18 @@ int orc_penalty_loss(const double *x, const double *y, int n, const double *pose
     free(qb);
     return ORC_OK;
 }
+
+/* Pixel centres of a raster grid, as the rasterisation call defines them:
+ * pixel (c, r) -> (fmaf(c, dx, x0), fmaf(r, dy, y0)), each rounded once to
+ * float32 (C's fmaf is the correctly rounded fused multiply-add).  Row-major
+ * xy pairs, out[2 (r W + c)]. */
+void orc_raster_centres(int W, int H, float x0, float y0, float dx, float dy, float *out)
+{
+    for (int r = 0; r < H; r++) {
+        const float cy = fmaf((float)r, dy, y0);
+        for (int c = 0; c < W; c++) {
+            out[2 * ((int64_t)r * W + c)] = fmaf((float)c, dx, x0);
+            out[2 * ((int64_t)r * W + c) + 1] = cy;
+        }
+    }
+}

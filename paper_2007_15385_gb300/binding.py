@@ -55,6 +55,9 @@ SIGNATURES = {
     "pip_test_single_noalloc": (_INT, [_P, _INT, _I32, _P, _INT, _I64, _P, _P, _P]),
     "pip_stream_variant_count": (_I32, []),
     "pip_selftest_wait_timeout": (_INT, [_P, _P, _I64, _P]),
+    "pip_raster_workspace_bytes": (ctypes.c_size_t, [_I32, _I32, _I32]),
+    "pip_rasterize": (_INT, [_P, _I32, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             _P, _P, _P, ctypes.c_size_t, _P]),
     "pip_batch_variant_count": (_I32, []),
     "pip_set_batch_variant": (_INT, [_P, _I32]),
     "pip_autotune_batch": (_INT, [_P, _P, _INT, _I64, _P, _P, _I32, _P, ctypes.POINTER(_I32),
@@ -345,6 +348,32 @@ def pip_test_host(tables: Tables, points_host: torch.Tensor, device_points: torc
 
 
 NOALLOC_MAX_POINTS = 1 << 20
+
+
+def pip_raster_workspace_bytes(num_polygons: int, width: int, height: int) -> int:
+    return int(lib().pip_raster_workspace_bytes(int(num_polygons), int(width), int(height)))
+
+
+def pip_rasterize(tables: Tables, width: int, height: int, x0: float, y0: float, dx: float, dy: float,
+                  first_hit: torch.Tensor | None = None, mask: torch.Tensor | None = None,
+                  workspace: torch.Tensor | None = None, want_ids: bool = True, want_mask: bool = True,
+                  stream=None):
+    """Pixel coverage: (ids int32 [height, width] or None, mask int32 [height, ceil(width / 32)] or None).
+    Pixel (c, r) has the float32 centre (fma(c, dx, x0), fma(r, dy, y0))."""
+    dev = tables.device
+    wpr = (width + 31) // 32
+    if want_ids and first_hit is None:
+        first_hit = torch.empty((height, width), dtype=torch.int32, device=dev)
+    if want_mask and mask is None:
+        mask = torch.empty((height, wpr), dtype=torch.int32, device=dev)
+    need = pip_raster_workspace_bytes(tables.num_polygons, width, height)
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+    _check(lib().pip_rasterize(tables, int(width), int(height), float(x0), float(y0), float(dx), float(dy),
+                               first_hit.data_ptr() if first_hit is not None else None,
+                               mask.data_ptr() if mask is not None else None, workspace.data_ptr(),
+                               workspace.numel() * workspace.element_size(), _stream(stream)), "pip_rasterize")
+    return first_hit, mask
 
 
 def pip_selftest_wait_timeout(tables: Tables, limit_cycles: int, stream=None) -> None:

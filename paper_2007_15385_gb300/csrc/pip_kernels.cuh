@@ -175,6 +175,11 @@ __device__ __forceinline__ void point_d(const void *pts, int dtype, int64_t i, d
 // Integer inputs: int64 cross products.  Otherwise: the fp64 Voronoi
 // comparison from the stored generators, and the exact orientation sign
 // where that comparison is within its bound.
+__device__ __noinline__ bool warp_inside_exact_xy(const PolyInfo &pi, int j, const double2 *__restrict__ g0tab,
+                                                  const double2 *__restrict__ gk,
+                                                  const void *__restrict__ verts, int vdtype, double px,
+                                                  double py);
+
 __device__ __noinline__ bool warp_inside_exact(const PolyInfo *__restrict__ poly, int j,
                                                const double2 *__restrict__ g0tab,
                                                const double2 *__restrict__ gk,
@@ -202,6 +207,21 @@ __device__ __noinline__ bool warp_inside_exact(const PolyInfo *__restrict__ poly
     }
     double px, py;
     point_d(pts, pdtype, i, px, py);
+    return warp_inside_exact_xy(pi, j, g0tab, gk, verts, vdtype, px, py);
+}
+
+// The same for a point given by its (float32-exact) coordinates; every lane
+// passes the same point.  Float path only (fp64 Voronoi, then exact
+// orientation for the edges it leaves open).
+__device__ __noinline__ bool warp_inside_exact_xy(const PolyInfo &pi, int j, const double2 *__restrict__ g0tab,
+                                                  const double2 *__restrict__ gk,
+                                                  const void *__restrict__ verts, int vdtype, double px,
+                                                  double py)
+{
+    const int lane = threadIdx.x & 31;
+    if (pi.status != PIP_OK) return false;
+    const int n = pi.n, v0 = pi.voff, sigma = pi.orient;
+    bool out = false;
     if (!isfinite(px) || !isfinite(py)) return false;
     const double2 g0 = g0tab[j];
     const double e = pi.gerr;

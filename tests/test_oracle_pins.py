@@ -538,3 +538,32 @@ def test_penalty_translation_invariance():
     assert l1 == pytest.approx(l0, rel=1e-12)
     np.testing.assert_allclose(gv1, gv0, rtol=1e-8, atol=1e-10)
     np.testing.assert_allclose(gp1, gp0, rtol=1e-8, atol=1e-10)
+
+
+def _round_f32(fr):
+    """Exact rational -> nearest float32, ties to even (checked against neighbours)."""
+    from fractions import Fraction
+    f = np.float32(float(fr))
+    best = None
+    for cand in (np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))):
+        d = abs(Fraction(float(cand)) - fr)
+        key = (d, int(np.frombuffer(np.float32(cand).tobytes(), np.uint32)[0]) & 1)
+        if best is None or key < best[0]:
+            best = (key, cand)
+    return best[1]
+
+
+def test_raster_centres_are_one_rounding_of_the_exact_grid():
+    from fractions import Fraction
+    rng = np.random.default_rng(21)
+    for _ in range(6):
+        x0, y0 = (np.float32(v) for v in rng.uniform(-1e4, 1e4, 2))
+        dx, dy = (np.float32(v) for v in rng.uniform(1e-3, 7.0, 2))
+        W, H = 37, 5
+        got = oracle.raster_centres(W, H, x0, y0, dx, dy).reshape(H, W, 2)
+        for c in range(W):
+            want = _round_f32(Fraction(c) * Fraction(float(dx)) + Fraction(float(x0)))
+            assert got[0, c, 0] == want
+        for r in range(H):
+            want = _round_f32(Fraction(r) * Fraction(float(dy)) + Fraction(float(y0)))
+            assert (got[r, :, 1] == want).all()
