@@ -311,9 +311,21 @@ __device__ __forceinline__ void vertex_d(const void *verts, int vdtype, int64_t 
 __device__ __forceinline__ bool inside_exact_int(const RefineArgs &A, int n, int v0, int sigma, int64_t i)
 {
     const int2 pq = ((const int2 *)A.pts)[i];
-    const int64_t px = pq.x, py = pq.y;
     const int2 *v = (const int2 *)A.verts + v0;
     int2 a = v[n - 1];
+    // -2^30 <= p < 2^30 per coordinate (unsigned compare: no abs overflow at INT_MIN)
+    if ((uint32_t)pq.x + (1u << 30) < (1u << 31) && (uint32_t)pq.y + (1u << 30) < (1u << 31)) {
+        // |v| <= 2^24: every difference fits in int32, each product is one
+        // 32 x 32 -> 64-bit multiply (|product| < 2^56), the cross product exact
+        for (int k = 0; k < n; ++k) {
+            const int2 b = v[k];
+            const int64_t cr = (int64_t)(b.x - a.x) * (pq.y - a.y) - (int64_t)(b.y - a.y) * (pq.x - a.x);
+            if ((cr > 0 ? 1 : (cr < 0 ? -1 : 0)) == -sigma) return false;
+            a = b;
+        }
+        return true;
+    }
+    const int64_t px = pq.x, py = pq.y;
     for (int k = 0; k < n; ++k) {
         const int2 b = v[k];
         // |b - a| <= 2^25 and |p - a| < 2^32 + 2^24: each product < 2^58

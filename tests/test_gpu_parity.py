@@ -255,6 +255,31 @@ def test_integer_points_beyond_float_range():
     assert_same(got, oracle_own(w), "big ints")
 
 
+def test_ragged_integer_points_at_the_int32_limits():
+    # the batch refine's int64 test: a fast path for |p| < 2^30 and a general
+    # one beyond; points at both sides of that limit and at the int32 extremes,
+    # many exactly on edges (integer polygons, integer points)
+    sq = np.array([[-1000, -1000], [1000, -1000], [1000, 1000], [-1000, 1000]], np.int32)
+    tri = np.array([[0, 0], [2 ** 24, 0], [0, 2 ** 24]], np.int32)
+    big = 2 ** 30
+    extreme = [[0, 0], [1000, 0], [1001, 0], [big - 1, 5], [big, 5], [-big, 0], [-big - 1, 0],
+               [-2 ** 31, 0], [2 ** 31 - 1, 2 ** 31 - 1], [1000, 1000], [-1000, -1001], [0, -1000]]
+    rng = np.random.default_rng(60)
+    on_edge = np.stack([rng.integers(0, 2 ** 24, 500), np.zeros(500, np.int64)], 1)
+    diag = rng.integers(0, 2 ** 24, 500)
+    on_hyp = np.stack([diag, 2 ** 24 - diag], 1)
+    pts_sq = np.array(extreme * 3, np.int64)
+    pts_tri = np.concatenate([np.array(extreme, np.int64), on_edge, on_hyp, on_hyp + [0, 1], on_hyp - [1, 0]])
+    pts = np.concatenate([pts_sq, pts_tri]).astype(np.int32)
+    verts = np.concatenate([sq, tri])
+    voffs = np.array([0, 4, 7], np.int32)
+    poffs = np.array([0, len(pts_sq), len(pts)], np.int64)
+    w = wl.Workload("int_limits", verts, voffs, pts, poffs)
+    got, _, refine, st = run_test(w)
+    assert st == B.PIP_OK and refine > 1000
+    assert_same(got, oracle_own(w), "int32 limits, batch")
+
+
 def test_nonfinite_points_are_outside():
     v = wl.regular_polygon(6, 1.0).astype(np.float32)
     pts = np.array([[0, 0], [np.nan, 0], [0, np.inf], [-np.inf, np.inf], [np.inf, np.inf],
