@@ -204,7 +204,7 @@ pip_status pip_autotune_stream(pip_tables *t, const void *d_points, pip_dtype pd
 /*
  * Tile shapes of the pipelined own-polygon batch kernel (the path pip_test
  * takes with point offsets and 16-byte aligned points): each variant is
- * (points per lane, ring stages); an item of work is 256 x points per lane
+ * (points per lane, ring stages); an item of work is 224 x points per lane
  * points of one polygon.  pip_autotune_batch times every variant `reps` times
  * with CUDA events on the caller's own batch (d_point_offsets as in pip_test;
  * synchronizes, not during capture), keeps the fastest in the tables and

@@ -8,7 +8,8 @@
 // offsets, writes the item table (items of one polygon are consecutive) and
 // zeroes the mask words that straddle two polygons' ranges.
 //
-// Persistent CTAs, one producer warp and eight consumer warps.  The producer
+// Persistent CTAs, one producer warp and seven consumer warps (16 warps per SM
+// at two CTAs: 128 registers a thread, 16 points per lane).  The producer
 // takes the next item from a global counter (dynamic balance: polygons have
 // 3 to 64 edges and 10^3 to 10^5 points) and bulk-copies into a ring stage:
 // the item's points, the polygon's padded coefficient row and its PolyInfo
@@ -37,7 +38,7 @@ struct RaggedHeader {
     int32_t rot, pad0, pad1, pad2;
 };
 
-constexpr int kRaggedWarps = 8;
+constexpr int kRaggedWarps = 7;  // consumer warps
 constexpr int kRaggedThreads = (kRaggedWarps + 1) * 32;
 
 template <int PPL, int STAGES>
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBl
                 h->lo = ci.lo;
                 h->hi = ci.hi;
                 h->rot = rot;
-                rot = (rot + (ci.hi - 1) / kSlice - ci.lo / kSlice + 1) & (kRaggedWarps - 1);
+                rot = (rot + (ci.hi - 1) / kSlice - ci.lo / kSlice + 1) % kRaggedWarps;
                 const uint32_t cbytes = (uint32_t)(kPadStride * sizeof(float4));
                 mbar_arrive_expect_tx(&full[s], pbytes + cbytes + (uint32_t)sizeof(PolyInfo));
                 if (pbytes) bulk_copy_g2s(st + (sa - c0) * 8, (const char *)pts + sa * 8, pbytes, &full[s]);
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBl
             const RaggedHeader h = *(const RaggedHeader *)(st + C::kHdrOff);
             if (h.j < 0) break;
             const int nsl = (h.hi - 1) / kSlice - h.lo / kSlice + 1;
-            const int r = (warp - h.rot) & (kRaggedWarps - 1);
+            const int r = (warp - h.rot + kRaggedWarps) % kRaggedWarps;
             if (r < nsl) {
                 const PolyInfo &pi = *(const PolyInfo *)(st + C::kInfoOff);
                 const int64_t c0 = (int64_t)h.k * kTile;

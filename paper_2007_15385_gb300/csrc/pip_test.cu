@@ -57,11 +57,11 @@ cudaError_t launch_ragged(const pip_tables *t, const void *pts, int64_t M, const
 
 // The pipelined own-polygon batch: setup (items, shared mask words, counters)
 // then the persistent kernel.  Variants: (points per lane, ring stages); the
-// item tile is 8 warps x 32 lanes x points per lane.
+// item tile is 7 consumer warps x 32 lanes x points per lane.
 struct BatchVariant {
     int ppl, stages;
 };
-constexpr BatchVariant kBatchVariants[] = {{12, 3}, {12, 4}, {8, 4}, {8, 6}};
+constexpr BatchVariant kBatchVariants[] = {{16, 3}, {16, 2}, {12, 3}, {12, 4}};
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
 template <int PPL, int STAGES, bool INT>
@@ -91,10 +91,10 @@ cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, c
                               uint32_t *mask, cudaStream_t s)
 {
     switch (t->batch_variant) {
-    case 1: return launch_ragged_tma_one<12, 4, INT>(t, pts, M, poffs, mask, s);
-    case 2: return launch_ragged_tma_one<8, 4, INT>(t, pts, M, poffs, mask, s);
-    case 3: return launch_ragged_tma_one<8, 6, INT>(t, pts, M, poffs, mask, s);
-    default: return launch_ragged_tma_one<12, 3, INT>(t, pts, M, poffs, mask, s);
+    case 1: return launch_ragged_tma_one<16, 2, INT>(t, pts, M, poffs, mask, s);
+    case 2: return launch_ragged_tma_one<12, 3, INT>(t, pts, M, poffs, mask, s);
+    case 3: return launch_ragged_tma_one<12, 4, INT>(t, pts, M, poffs, mask, s);
+    default: return launch_ragged_tma_one<16, 3, INT>(t, pts, M, poffs, mask, s);
     }
 }
 
@@ -510,10 +510,10 @@ int stream_variant_count() { return kNumStreamVariants; }
 
 cudaError_t ragged_kernels_setup()
 {
-    cudaError_t e = set_ragged_attr<12, 3>();
+    cudaError_t e = set_ragged_attr<16, 3>();
+    if (e == cudaSuccess) e = set_ragged_attr<16, 2>();
+    if (e == cudaSuccess) e = set_ragged_attr<12, 3>();
     if (e == cudaSuccess) e = set_ragged_attr<12, 4>();
-    if (e == cudaSuccess) e = set_ragged_attr<8, 4>();
-    if (e == cudaSuccess) e = set_ragged_attr<8, 6>();
     return e;
 }
 
