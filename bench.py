@@ -46,7 +46,7 @@ KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_stream_tma.cuh",
                   "paper_2007_15385_gb300/csrc/pip_tma.cuh",
                   "paper_2007_15385_gb300/csrc/pip_kernels.cuh",
                   "paper_2007_15385_gb300/csrc/pip_internal.cuh",
-                  "paper_2007_15385_gb300/csrc/pip_test.cu"]
+                  "paper_2007_15385_gb300/csrc/pip_stream.cu"]
 
 
 def sources_sha() -> str:

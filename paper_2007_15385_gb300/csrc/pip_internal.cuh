@@ -143,6 +143,9 @@ cudaError_t stream_kernels_setup();
 cudaError_t ragged_kernels_setup();
 cudaError_t allpairs_setup();
 int stream_variant_count();
+// the pipelined single-polygon test (pip_stream.cu): one launch, refine inline
+cudaError_t launch_stream_pipelined(const pip_tables *t, const void *pts, bool ints, int64_t M, uint32_t *mask,
+                                    cudaStream_t s);
 }  // namespace pip
 
 namespace pip {
