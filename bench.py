@@ -41,11 +41,12 @@ FALLBACK_HBM_GBS = 6800.0
 # workload, from one ncu capture (profiles/stream_tma_kernel_vehicle_footprint.md)
 # of 2^25 points scaled by 2 to the 2^26-point launch,
 # valid only while the kernel sources hash to the value recorded with it.
-NCU_TRAFFIC = {"bytes": 549181440, "sources_sha": "6580d146d0104200"}
+NCU_TRAFFIC = {"bytes": 549279744, "sources_sha": "b6c28949ca6f3692"}
 KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_stream_tma.cuh",
                   "paper_2007_15385_gb300/csrc/pip_tma.cuh",
                   "paper_2007_15385_gb300/csrc/pip_kernels.cuh",
                   "paper_2007_15385_gb300/csrc/pip_internal.cuh",
+                  "paper_2007_15385_gb300/csrc/pip_stream_launch.cuh",
                   "paper_2007_15385_gb300/csrc/pip_stream.cu"]
 
 

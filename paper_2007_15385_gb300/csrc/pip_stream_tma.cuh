@@ -65,7 +65,7 @@ struct SliceCtx {
 // the slice's PPL mask words, queue the uncertain points.  TAIL: the slice may
 // run past M (or hold the odd last point, which is not in the bulk copy).
 // CENTER: subtract the local origin o (false when o = (0, 0)).
-template <int NE, int PPL, bool INT, bool MIN3, bool CENTER, bool TAIL>
+template <int NE, int PPL, bool INT, bool CENTER, bool TAIL>
 __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned char *stage,
                                               const void *__restrict__ pts, int64_t M, int64_t wfirst,
                                               int lane, uint32_t *__restrict__ mask, bool vec_store,
@@ -181,8 +181,7 @@ __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned
 
 // NE > 0: the polygon has at most NE edges and the coefficients live in
 // registers; NE == 0: any edge count, coefficients read from shared memory.
-// MIN3: take the running min three operands at a time.
-template <int NE, int PPL, int STAGES, bool INT, bool MIN3>
+template <int NE, int PPL, int STAGES, bool INT>
 __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBlocks) stream_tma_kernel(
     const __grid_constant__ StreamPoly sp, const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
     const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab,
@@ -276,13 +275,13 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
             const bool whole = wfirst + 32 * PPL <= whole_end;
             if (whole) {
                 if (center)
-                    consume_slice<NE, PPL, INT, MIN3, true, false>(cx, stage, pts, M, wfirst, lane, mask,
+                    consume_slice<NE, PPL, INT, true, false>(cx, stage, pts, M, wfirst, lane, mask,
                                                                    vec_store, myqueue, &s_refined);
                 else
-                    consume_slice<NE, PPL, INT, MIN3, false, false>(cx, stage, pts, M, wfirst, lane, mask,
+                    consume_slice<NE, PPL, INT, false, false>(cx, stage, pts, M, wfirst, lane, mask,
                                                                     vec_store, myqueue, &s_refined);
             } else {
-                consume_slice<NE, PPL, INT, MIN3, true, true>(cx, stage, pts, M, wfirst, lane, mask,
+                consume_slice<NE, PPL, INT, true, true>(cx, stage, pts, M, wfirst, lane, mask,
                                                               vec_store, myqueue, &s_refined);
             }
             __syncwarp();

@@ -280,6 +280,37 @@ def test_ragged_integer_points_at_the_int32_limits():
     assert_same(got, oracle_own(w), "int32 limits, batch")
 
 
+@pytest.mark.parametrize("shape", ["footprint", "needle"])
+def test_single_bound_around_the_l1_ball_and_far_away(shape):
+    """The one-polygon kernel decides with one bound per polygon when prepare
+    proves it valid (a convex polygon whose smallest angle and generator
+    distances are not tiny) and with the per-point bound otherwise (the needle:
+    a 1e-6 rad vertex).  Points just beyond each vertex (where |x| + |y| leaves
+    the vertices' L1 ball), along rays out to huge distances, and on a grid."""
+    rng = np.random.default_rng(61)
+    if shape == "footprint":
+        v = wl.vehicle_footprint(m=16).vertices
+    else:
+        v = np.array([[0, 0], [1000, 0], [1000, 0.001]], np.float32)
+    c = v.astype(np.float64).mean(0)
+    pts = []
+    for p in v.astype(np.float64):
+        d = p - c
+        for s in (1 + 2.0 ** -np.arange(1, 24)).tolist() + [1 - 2.0 ** -20, 1.0, 1.5, 3.0]:
+            pts.append(c + s * d)
+            pts.append(c + s * d + rng.normal(0, 1e-6, 2) * np.abs(d).max())
+    for ang in rng.uniform(0, 2 * np.pi, 200):
+        for r in (10.0, 1e3, 1e6, 1e12, 1e30):
+            pts.append(c + r * np.array([np.cos(ang), np.sin(ang)]))
+    big = np.float32(3.4e38)
+    pts += [[big, big], [-big, big], [big, 0], [0, -big]]
+    lo, hi = v.min(0) - 1.0, v.max(0) + 1.0
+    pts += list(rng.uniform(lo, hi, size=(50_000, 2)))
+    w = wl.Workload("l1ball", v, np.array([0, len(v)], np.int32), np.array(pts, np.float32))
+    got, _, _, st = run_test(w)
+    assert_same(got, oracle_own(w), "single bound, %s" % shape)
+
+
 def test_nonfinite_points_are_outside():
     v = wl.regular_polygon(6, 1.0).astype(np.float32)
     pts = np.array([[0, 0], [np.nan, 0], [0, np.inf], [-np.inf, np.inf], [np.inf, np.inf],
