@@ -336,14 +336,34 @@ def unpack_mask(mask: torch.Tensor, num_points: int) -> torch.Tensor:
 
 
 def pip_test_host(tables: Tables, points_host: torch.Tensor, device_points: torch.Tensor,
-                  device_mask: torch.Tensor, mask_host: torch.Tensor, stream=None):
-    """End-to-end call on host buffers: pinned host points -> device, pip_test, mask -> pinned
-    host.  The caller provides the device staging buffers, so nothing is allocated per call."""
+                  device_mask: torch.Tensor, mask_host: torch.Tensor, stream=None, chunks: int = 8):
+    """End-to-end call on host buffers (one polygon or all pairs, mask only): pinned host
+    points -> device, pip_test, mask -> pinned host, in `chunks` pieces so that the copy of
+    one piece overlaps the test and the read-back of the previous one.  The caller provides
+    the device staging buffers, so nothing is allocated per call.  Pieces start at multiples
+    of 128 points (whole, 16-byte aligned mask words) and are tested in order on `stream`
+    (they share the tables' refine queue); the copies run on a second stream."""
     s = stream if stream is not None else torch.cuda.current_stream()
-    with torch.cuda.stream(s):
-        device_points.copy_(points_host, non_blocking=True)
-        pip_test(tables, device_points, mask=device_mask, stream=s)
-        mask_host.copy_(device_mask, non_blocking=True)
+    M = points_host.numel() // 2
+    piece = max(128, -(-M // max(1, int(chunks)) // 128) * 128)
+    cs = getattr(tables, "_copy_stream", None)
+    if cs is None or cs.device != device_points.device:
+        cs = torch.cuda.Stream(device=device_points.device)
+        tables._copy_stream = cs
+    cs.wait_stream(s)  # the staging buffers are free once earlier work on `stream` is done
+    hp = points_host.view(-1)
+    dp = device_points.view(-1)
+    for a in range(0, M, piece):
+        b = min(M, a + piece)
+        with torch.cuda.stream(cs):
+            dp[2 * a:2 * b].copy_(hp[2 * a:2 * b], non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(cs)
+        s.wait_event(ready)
+        with torch.cuda.stream(s):
+            w0, w1 = a // 32, (b + 31) // 32
+            pip_test(tables, dp[2 * a:2 * b], mask=device_mask[w0:w1], stream=s)
+            mask_host[w0:w1].copy_(device_mask[w0:w1], non_blocking=True)
     return mask_host
 
 

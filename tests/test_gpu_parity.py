@@ -311,6 +311,25 @@ def test_single_bound_around_the_l1_ball_and_far_away(shape):
     assert_same(got, oracle_own(w), "single bound, %s" % shape)
 
 
+@pytest.mark.parametrize("chunks", [1, 3, 8])
+def test_host_call_in_pieces_matches_the_oracle(chunks):
+    w = wl.vehicle_footprint(m=1_000_003)
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                      max_points=w.num_points)
+    ph = torch.from_numpy(w.points).pin_memory()
+    pd = torch.empty(w.points.shape, dtype=torch.float32, device=dev())
+    nw = (w.num_points + 31) // 32
+    md = torch.empty(nw, dtype=torch.int32, device=dev())
+    mh = torch.full((nw,), -1, dtype=torch.int32).pin_memory()
+    B.pip_test_host(t, ph, pd, md, mh, chunks=chunks)
+    torch.cuda.synchronize()
+    words = mh.numpy().view(np.uint32)
+    assert words[-1] >> (w.num_points % 32) == 0
+    got = np.unpackbits(words.view(np.uint8), bitorder="little")[:w.num_points]
+    assert_same(got, oracle_own(w), "host call, %d pieces" % chunks)
+    t.close()
+
+
 def test_nonfinite_points_are_outside():
     v = wl.regular_polygon(6, 1.0).astype(np.float32)
     pts = np.array([[0, 0], [np.nan, 0], [0, np.inf], [-np.inf, np.inf], [np.inf, np.inf],
