@@ -151,6 +151,33 @@ def test_gis_batch_unaligned_points():
     assert_same(got, oracle_own(w), "gis unaligned")
 
 
+@pytest.mark.parametrize("n", [4, 12, 16, 40])
+def test_every_stream_variant_matches_the_oracle_and_autotune_picks_one(n):
+    # every tile shape of the one-polygon kernel, for each edge-count variant
+    # (registers up to 16 edges, shared memory above), ragged tail included
+    rng = np.random.default_rng(70 + n)
+    v = wl._circle_polygon(rng, n, 0.5, -0.25, 2.4, 1.0)
+    pts = rng.uniform(-3.0, 3.0, size=(200_003, 2)).astype(np.float32)
+    w = wl.Workload("variants", v, np.array([0, n], np.int32), pts)
+    want = oracle_own(w)
+    t = B.pip_prepare(torch.from_numpy(v).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                      max_points=w.num_points)
+    p = torch.from_numpy(pts).to(dev())
+    mbuf, mask = guarded((w.num_points + 31) // 32)
+    for var in range(B.pip_stream_variant_count()):
+        B.pip_set_stream_variant(t, var)
+        mask.fill_(-1)
+        B.pip_test(t, p, mask=mask)
+        st, _ = B.pip_get_status(t)
+        assert st == B.PIP_OK
+        check_guards(mbuf)
+        got = np.unpackbits(mask.cpu().numpy().view(np.uint8), bitorder="little")[:w.num_points]
+        assert_same(got, want, "stream variant %d, %d edges" % (var, n))
+    best, ms = B.pip_autotune_stream(t, p, mask, reps=2)
+    assert 0 <= best < B.pip_stream_variant_count() and ms > 0
+    t.close()
+
+
 @pytest.mark.parametrize("ints", [False, True])
 def test_every_batch_variant_matches_the_oracle_and_autotune_picks_one(ints):
     w = (wl.integer_hulls(seed=20, num_polygons=24, points_per_polygon=2000) if ints
