@@ -45,6 +45,8 @@ MUTANTS = {
                                    "double mu = (G0x * g0x + G0y * g0y) / S;"),
     "penalty_sigmoid_sign": ("double gm = -sigmoid(-best / tau) / tau;",
                              "double gm = -sigmoid(best / tau) / tau;"),
+    "raster_centre_two_roundings": ("= fmaf((float)c, dx, x0);", "= (float)c * dx + x0;"),
+    "raster_row_spacing": ("fmaf((float)r, dy, y0);", "fmaf((float)r, dx, y0);"),
 }
 
 
