@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -119,18 +120,58 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline_run(w, sample: int) -> dict:
-    """The oracle (exact predicate, one thread) on the first `sample` points."""
+    """The oracle on the first `sample` points: the exact predicate on one
+    thread (the value), the same on every host core (contiguous pieces, one
+    per thread; the C calls release the GIL) and the literal fp64 Alg. 5 on
+    one thread."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
     pts = np.ascontiguousarray(w.points[:sample])
     n = int(w.edges()[0])
     oracle.inside_exact(w.vertices, pts[:1024])  # build + warm
     t0 = time.perf_counter()
     oracle.inside_exact(w.vertices, pts)
     dt = time.perf_counter() - t0
+    threads = os.cpu_count() or 1
+    pieces = np.array_split(pts, threads)
+    with ThreadPoolExecutor(threads) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda q: oracle.inside_exact(w.vertices, np.ascontiguousarray(q)), pieces))
+        dt_all = time.perf_counter() - t0
+    half = pts[:sample // 2]
+    t0 = time.perf_counter()
+    oracle.voronoi_fp64(w.vertices, half)
+    dt_f64 = time.perf_counter() - t0
     return {"value": sample * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "first %d of the %d points, oracle.inside_exact (exact orientation "
-                      "predicate, early exit per point), single thread, %.2f s" % (sample, len(w.points), dt)}
+                      "predicate, early exit per point), single thread, %.2f s" % (sample, len(w.points), dt),
+            "cpu_model": cpu_model(),
+            "all_cores": {"value": sample * n / dt_all / 1e9, "cores": threads,
+                          "sample": "the same points in %d contiguous pieces, one per thread, %.2f s"
+                                    % (threads, dt_all)},
+            "plain_fp64_alg5": {"value": len(half) * n / dt_f64 / 1e9, "cores": 1,
+                                "sample": "first %d points, oracle.voronoi_fp64 (Alg. 5 in fp64 with "
+                                          "its own ambiguity flag), single thread, %.2f s" % (len(half), dt_f64)}}
 
 
 def run_reference(args):

@@ -57,3 +57,12 @@ def test_shards_share_the_footprint_but_not_the_points():
     np.testing.assert_array_equal(a.vertices, c.vertices)
     assert not np.array_equal(a.points, b.points)
     assert not np.array_equal(b.points, c.points)
+
+
+def test_cpu_baseline_reports_one_thread_all_cores_and_plain_fp64():
+    w = wl.vehicle_footprint(m=1 << 14)
+    r = bench.cpu_baseline_run(w, 1 << 13)
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
+    assert r["all_cores"]["cores"] == (os.cpu_count() or 1) and r["all_cores"]["value"] > 0
+    assert r["plain_fp64_alg5"]["cores"] == 1 and r["plain_fp64_alg5"]["value"] > 0
+    assert isinstance(r["cpu_model"], str) and r["cpu_model"]
