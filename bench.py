@@ -589,7 +589,7 @@ def run_other(args):
                  "forward_Gtests_per_s": tests / (fwd * 1e-3) / 1e9,
                  "backward_Gtests_per_s": tests / (bwd * 1e-3) / 1e9,
                  "pairs": len(poses) * M}
-        launches = 4
+        launches = 5  # begin, prepare, pose coefficients, penalty, loss reduction
     else:
         t = B.pip_prepare(v, vo, max_points=M)
         mode = B.PIP_MASK | (B.PIP_FIRST_HIT if args.workload == "gis_all_pairs" else 0)

@@ -16,10 +16,13 @@
 // points.  At block start one thread per edge folds the pose into the edge's
 // coefficients (fp64, rounded once), so that a margin term is two FMAs on the
 // world point; for up to 16 edges the coefficients then sit in registers.
-// Every thread keeps float32 partial sums (the backward pass's per-edge sums
-// go to per-warp shared-memory slots by atomics), the block reduces them in
-// fp64 into its own slot of the workspace, and a final kernel adds the slots
-// in a fixed order.
+// Every thread keeps float32 partial sums, the block reduces them in fp64
+// into its own slot of the workspace, and a final kernel adds the slots in a
+// fixed order.  In the backward pass only the (pose, point) pairs with a
+// nonzero gradient (the points within ~87 tau of the footprint, where the
+// float32 sigmoid has not underflowed) need the argmax edge and the per-edge
+// sums; each warp queues those pairs in shared memory and resolves them 32
+// at a time, so that a warp does not take that path for a single near point.
 #include <stdlib.h>
 
 #include "pip_prepare_kernel.cuh"
@@ -201,7 +204,43 @@ __host__ __device__ constexpr int lane_words() { return NE > 0 ? 3 * NE + 1 : 3 
 template <int NE>
 __host__ __device__ constexpr int acc_rows() { return NE > 0 ? kPenThreads : kPenThreads / 32; }
 template <int NE>
-constexpr size_t acc_bytes() { return (size_t)acc_rows<NE>() * lane_words<NE>() * sizeof(float); }
+__host__ __device__ constexpr size_t acc_floats() { return (size_t)acc_rows<NE>() * lane_words<NE>(); }
+// per-warp ring of queued pairs (dx, dy, dL/dm, m) after the accumulators
+constexpr int kPenQueue = 64;
+template <int NE>
+constexpr size_t acc_bytes()
+{
+    return acc_floats<NE>() * sizeof(float) + (size_t)(kPenThreads / 32) * kPenQueue * sizeof(float4);
+}
+
+// One queued pair: the lowest edge whose term equals the max m takes the
+// gradient g (the subgradient of the max); its slot gathers g, g dx, g dy.
+template <int NE>
+__device__ __forceinline__ void pen_scatter(const float4 *cs, const float (&w)[NE > 0 ? NE : 1][3], int n,
+                                            float *my, float4 e)
+{
+    int kb = 0;
+    if (NE > 0) {
+#pragma unroll
+        for (int k = (NE > 0 ? NE : 1) - 1; k >= 0; --k)
+            if (fmaf(e.x, w[k][0], fmaf(e.y, w[k][1], -w[k][2])) == e.w) kb = k;
+    } else {
+        for (int k = n - 1; k >= 0; --k) {
+            const float4 c = cs[k];
+            if (fmaf(e.x, c.x, fmaf(e.y, c.y, -c.z)) == e.w) kb = k;
+        }
+    }
+    float *slot = my + 3 * kb;
+    if (NE > 0) {
+        slot[0] += e.z;
+        slot[1] += e.z * e.x;
+        slot[2] += e.z * e.y;
+    } else {
+        atomicAdd(&slot[0], e.z);
+        atomicAdd(&slot[1], e.z * e.x);
+        atomicAdd(&slot[2], e.z * e.y);
+    }
+}
 
 template <int NE, bool BACKWARD>
 __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
@@ -211,7 +250,7 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
     double *__restrict__ edge_part)
 {
     constexpr int kWarps = kPenThreads / 32;
-    extern __shared__ float lane_acc[];  // backward: [kPenThreads][kLaneWords]
+    extern __shared__ float lane_acc[];  // backward: [acc_rows][kLW] accumulators, then the warps' queues
     __shared__ double red[kWarps];
     const int n = poly[0].status == PIP_OK ? poly[0].n : 0;
     const int pose = blockIdx.y;
@@ -237,6 +276,7 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
     const int64_t p0 = (int64_t)blockIdx.x * kPenPoints;
     const int64_t p1 = min(p0 + kPenPoints, M);
     constexpr int64_t kStep = (int64_t)kPenThreads * kPenUnroll;
+    const int lane = threadIdx.x & 31;
     auto load = [&](int64_t i0, float2 (&p)[kPenUnroll]) {
 #pragma unroll
         for (int u = 0; u < kPenUnroll; ++u) {
@@ -244,51 +284,51 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
             p[u] = i < p1 ? ((const float2 *)pts)[i] : make_float2(ftx, fty);
         }
     };
+    // backward: this warp's queue; head and tail count pairs (warp-uniform)
+    float4 *q = (float4 *)(lane_acc + acc_floats<NE>()) + (threadIdx.x >> 5) * kPenQueue;
+    int qh = 0, qt = 0;
     if (n > 0) {
+        // the trip count depends on the warp's first point only, so that the
+        // whole warp takes part in every ballot
+        const int64_t wbase = p0 + (threadIdx.x & ~31);
         float2 nxt[kPenUnroll];
-        load(p0 + threadIdx.x, nxt);
-        for (int64_t i0 = p0 + threadIdx.x; i0 < p1; i0 += kStep) {
+        load(wbase + lane, nxt);
+        for (int64_t b0 = wbase; b0 < p1; b0 += kStep) {
             float2 p[kPenUnroll];
 #pragma unroll
             for (int u = 0; u < kPenUnroll; ++u) p[u] = nxt[u];
-            load(i0 + kStep, nxt);  // the next points are in flight while these are evaluated
+            load(b0 + kStep + lane, nxt);  // the next points are in flight while these are evaluated
 #pragma unroll
             for (int u = 0; u < kPenUnroll; ++u) {
-                if (i0 + (int64_t)u * kPenThreads >= p1) continue;
+                const bool valid = b0 + lane + (int64_t)u * kPenThreads < p1;
                 const float dx = p[u].x - ftx, dy = p[u].y - fty;
                 const float m = margin_of<NE>(cs, w, n, dx, dy);
                 const float z = -m * inv_tau;
                 const float e = exp_neg_abs(z);
                 if (!BACKWARD) {
-                    l_acc += fmaxf(z, 0.f) + log1p_small(e);  // softplus(z)
+                    if (valid) l_acc += fmaxf(z, 0.f) + log1p_small(e);  // softplus(z)
                 } else {
                     const float g = -sigmoid_from(z, e) * inv_tau;  // dL/dm
-                    if (g != 0.f) {
-                        // the lowest edge that attains the max
-                        int kb = 0;
-                        if (NE > 0) {
-#pragma unroll
-                            for (int k = (NE > 0 ? NE : 1) - 1; k >= 0; --k)
-                                if (fmaf(dx, w[k][0], fmaf(dy, w[k][1], -w[k][2])) == m) kb = k;
-                        } else {
-                            for (int k = n - 1; k >= 0; --k) {
-                                const float4 c = cs[k];
-                                if (fmaf(dx, c.x, fmaf(dy, c.y, -c.z)) == m) kb = k;
-                            }
-                        }
-                        float *slot = my + 3 * kb;
-                        if (NE > 0) {
-                            slot[0] += g;
-                            slot[1] += g * dx;
-                            slot[2] += g * dy;
-                        } else {
-                            atomicAdd(&slot[0], g);
-                            atomicAdd(&slot[1], g * dx);
-                            atomicAdd(&slot[2], g * dy);
+                    const bool hot = valid && g != 0.f;
+                    const unsigned bal = __ballot_sync(0xffffffffu, hot);
+                    if (bal) {
+                        if (hot)
+                            q[(qt + __popc(bal & ((1u << lane) - 1u))) & (kPenQueue - 1)] =
+                                make_float4(dx, dy, g, m);
+                        qt += __popc(bal);
+                        if (qt - qh >= 32) {  // at most 63 queued: the ring never overflows
+                            __syncwarp();
+                            pen_scatter<NE>(cs, w, n, my, q[(qh + lane) & (kPenQueue - 1)]);
+                            qh += 32;
+                            __syncwarp();  // drained slots are refilled next
                         }
                     }
                 }
             }
+        }
+        if (BACKWARD) {
+            __syncwarp();
+            if (lane < qt - qh) pen_scatter<NE>(cs, w, n, my, q[(qh + lane) & (kPenQueue - 1)]);
         }
     }
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
@@ -300,7 +340,7 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
         // per (edge, component) v: warp v % 8 adds the 256 lanes' slots, 8 per
         // lane then a shuffle tree (float32, fixed order)
         __shared__ double es[kMaxEdges][3];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int wid = threadIdx.x >> 5;
         for (int v = wid; v < 3 * kMaxEdges; v += kWarps) {
             float t = 0.f;
             if (v < 3 * n)
@@ -480,13 +520,16 @@ void launch_penalty(int n, dim3 grid, cudaStream_t s, const PenWorkspace &w, con
 {
     const int P = (int)grid.y;
     pose_coef_kernel<<<P, 64, 0, s>>>(w.poly, w.coefn, poses, P, w.pose_coef, w.pose_rot);
-    // 16 edges need 49 KiB of accumulators: above the default dynamic limit
-    if (BACKWARD && n > 12 && n <= 16)
-        cudaFuncSetAttribute(penalty_kernel<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)acc_bytes<16>());
+    // the backward pass's accumulators and queues (up to 57 KiB at 16 edges)
+    // with the static reduction buffers pass the default 48 KiB limit
 #define PIP_PEN(NE)                                                                                     \
-    penalty_kernel<NE, BACKWARD><<<grid, kPenThreads, BACKWARD ? acc_bytes<NE>() : 0, s>>>(              \
-        w.poly, w.pose_coef, w.pose_rot, poses, pts, M, n, tau, w.loss_part, w.pose_part, w.edge_part)
+    do {                                                                                                \
+        if (BACKWARD)                                                                                   \
+            cudaFuncSetAttribute(penalty_kernel<NE, BACKWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)acc_bytes<NE>());                                                 \
+        penalty_kernel<NE, BACKWARD><<<grid, kPenThreads, BACKWARD ? acc_bytes<NE>() : 0, s>>>(          \
+            w.poly, w.pose_coef, w.pose_rot, poses, pts, M, n, tau, w.loss_part, w.pose_part, w.edge_part); \
+    } while (0)
     if (n <= 4) PIP_PEN(4);
     else if (n <= 8) PIP_PEN(8);
     else if (n <= 12) PIP_PEN(12);

@@ -146,3 +146,25 @@ def test_penalty_full_size_sampled_poses():
         ok, nrm, bad = _rel_ok(gp[j], ref_gp[0], floor_frac=1e-2)
         assert ok, "pose %d: norm-wise %.2e, got %s want %s" % (j, nrm, gp[j], ref_gp[0])
     assert np.isfinite(gv.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("n", [12, 20])
+def test_penalty_every_pair_near_the_footprint(n):
+    """Poses near the origin and points within 3 m of it: every (pose, point)
+    pair has a nonzero gradient, so every warp's queue fills on every step
+    (the benchmark's trajectory has ~6 % such pairs)."""
+    w = wl.footprint_trajectory(seed=60 + n, m=16, num_poses=2, n=n)
+    rng = np.random.default_rng(61)
+    P = np.stack([rng.uniform(-0.3, 0.3, 6), rng.uniform(-0.3, 0.3, 6), rng.uniform(-3.1, 3.1, 6)],
+                 axis=1).astype(np.float32)
+    q = rng.uniform(-3.0, 3.0, size=(5003, 2)).astype(np.float32)
+    v, tau = w.vertices, w.extra["tau"]
+    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau).item()
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    ref_loss, ref_gv, ref_gp = oracle.penalty(v.astype(np.float64), P.astype(np.float64),
+                                             q.astype(np.float64), tau)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
+    assert ok, "n=%d vertex gradient: norm-wise %.2e, %d elements off" % (n, nrm, bad)
+    ok, nrm, bad = _rel_ok(gp.cpu().numpy(), ref_gp, floor_frac=1e-2)
+    assert ok, "n=%d pose gradient: norm-wise %.2e, %d elements off" % (n, nrm, bad)
