@@ -202,6 +202,19 @@ __device__ __forceinline__ int x_add_product(double *h, int len, double a, doubl
 static __device__ __noinline__ int orient_sign_exact(double ax, double ay, double bx, double by,
                                               double cx, double cy)
 {
+    // First stage of the same paper's adaptive predicate: the determinant
+    // rounded in fp64, (ax - cx)(by - cy) - (ay - cy)(bx - cx), has the exact
+    // sign whenever its magnitude exceeds (3 + 16 eps) eps times the sum of
+    // the two products' magnitudes (eps = 2^-53; the paper's bound for this
+    // evaluation order).  Only the rest falls through to the exact expansion.
+    {
+        const double l = __dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy));
+        const double r = __dmul_rn(__dsub_rn(ay, cy), __dsub_rn(bx, cx));
+        const double det = __dsub_rn(l, r);
+        const double bound = (3.0 + 16.0 * 0x1p-53) * 0x1p-53 * __dadd_rn(fabs(l), fabs(r));
+        if (det > bound) return 1;
+        if (-det > bound) return -1;
+    }
     double u1, u0, v1, v0, w1, w0, z1, z0;
     x_two_diff(bx, ax, u1, u0);  // bx - ax = u1 + u0
     x_two_diff(cy, ay, v1, v0);  // cy - ay

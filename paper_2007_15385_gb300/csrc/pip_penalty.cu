@@ -40,16 +40,19 @@ struct PenWorkspace {
     double2 *gk;
     float4 *coef;
     float4 *coefn;
-    double *loss_part;  // [blocks]
-    double *pose_part;  // [blocks][3]  dL/d(t_x, t_y, theta) of the block's pose, its points only
-    double *edge_part;  // [blocks][n][3]  (sum g, sum g x, sum g y) per argmax edge
-    double *edge_sum;   // [n][3]  reduced
-    double *pose_sum;   // [P][3]  reduced
+    double *loss_part;   // [blocks]
+    double *loss_stage;  // [ceil(blocks / kRedPer)]  first-level sums of loss_part
+    double *pose_part;   // [3][blocks]  dL/d(t_x, t_y, theta) of the block's pose, its points only
+    double *edge_part;   // [n][3][blocks]  (sum g, sum g x, sum g y) per argmax edge
+    double *edge_stage;  // [n][3][kEdgeChunks]  first-level sums of edge_part
+    double *pose_sum;    // [3][P]  reduced
     float4 *pose_coef;  // [P][kPoseStride]  per-pose affine forms (w'_x, w'_y, t', 0)
     double2 *pose_rot;  // [P]  (cos theta, sin theta)
 };
 
 constexpr int kPoseStride = kMaxEdges;
+constexpr int kRedPer = 2048;     // loss partials per first-level reduction block
+constexpr int kEdgeChunks = 16;   // first-level reduction blocks per edge sum
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -69,9 +72,10 @@ size_t carve(void *base, int n, int P, int64_t blocks, PenWorkspace *w)
     w->coef = (float4 *)take((size_t)n * sizeof(float4));
     w->coefn = (float4 *)take((size_t)n * sizeof(float4));
     w->loss_part = (double *)take((size_t)blocks * sizeof(double));
+    w->loss_stage = (double *)take((size_t)((blocks + kRedPer - 1) / kRedPer) * sizeof(double));
     w->pose_part = (double *)take((size_t)blocks * 3 * sizeof(double));
     w->edge_part = (double *)take((size_t)blocks * n * 3 * sizeof(double));
-    w->edge_sum = (double *)take((size_t)n * 3 * sizeof(double));
+    w->edge_stage = (double *)take((size_t)n * 3 * kEdgeChunks * sizeof(double));
     w->pose_sum = (double *)take((size_t)P * 3 * sizeof(double));
     w->pose_coef = (float4 *)take((size_t)P * kPoseStride * sizeof(float4));
     w->pose_rot = (double2 *)take((size_t)P * sizeof(double2));
@@ -172,6 +176,11 @@ __global__ void __launch_bounds__(64) pose_coef_kernel(const PolyInfo *__restric
 // any edge count, read from shared memory.  kPenUnroll points per thread in
 // flight.
 constexpr int kPenUnroll = 4;
+
+template <bool B>
+struct BoolTag {
+    static constexpr bool value = B;
+};
 
 template <int NE>
 __device__ __forceinline__ float margin_of(const float4 *cs, const float (&w)[NE > 0 ? NE : 1][3], int n,
@@ -274,64 +283,78 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
 
     float l_acc = 0.f;
     const int64_t p0 = (int64_t)blockIdx.x * kPenPoints;
-    const int64_t p1 = min(p0 + kPenPoints, M);
-    constexpr int64_t kStep = (int64_t)kPenThreads * kPenUnroll;
+    const int cnt = (int)(min(p0 + kPenPoints, M) - p0);  // this block's points
+    const float2 *bp = (const float2 *)pts + p0;
+    constexpr int kStep = kPenThreads * kPenUnroll;
     const int lane = threadIdx.x & 31;
-    auto load = [&](int64_t i0, float2 (&p)[kPenUnroll]) {
-#pragma unroll
-        for (int u = 0; u < kPenUnroll; ++u) {
-            const int64_t i = i0 + (int64_t)u * kPenThreads;
-            p[u] = i < p1 ? ((const float2 *)pts)[i] : make_float2(ftx, fty);
-        }
-    };
     // backward: this warp's queue; head and tail count pairs (warp-uniform)
     float4 *q = (float4 *)(lane_acc + acc_floats<NE>()) + (threadIdx.x >> 5) * kPenQueue;
     int qh = 0, qt = 0;
-    if (n > 0) {
-        // the trip count depends on the warp's first point only, so that the
-        // whole warp takes part in every ballot
-        const int64_t wbase = p0 + (threadIdx.x & ~31);
-        float2 nxt[kPenUnroll];
-        load(wbase + lane, nxt);
-        for (int64_t b0 = wbase; b0 < p1; b0 += kStep) {
-            float2 p[kPenUnroll];
-#pragma unroll
-            for (int u = 0; u < kPenUnroll; ++u) p[u] = nxt[u];
-            load(b0 + kStep + lane, nxt);  // the next points are in flight while these are evaluated
-#pragma unroll
-            for (int u = 0; u < kPenUnroll; ++u) {
-                const bool valid = b0 + lane + (int64_t)u * kPenThreads < p1;
-                const float dx = p[u].x - ftx, dy = p[u].y - fty;
-                const float m = margin_of<NE>(cs, w, n, dx, dy);
-                const float z = -m * inv_tau;
-                const float e = exp_neg_abs(z);
-                if (!BACKWARD) {
-                    if (valid) l_acc += fmaxf(z, 0.f) + log1p_small(e);  // softplus(z)
-                } else {
-                    const float g = -sigmoid_from(z, e) * inv_tau;  // dL/dm
-                    const bool hot = valid && g != 0.f;
-                    const unsigned bal = __ballot_sync(0xffffffffu, hot);
-                    if (bal) {
-                        if (hot)
-                            q[(qt + __popc(bal & ((1u << lane) - 1u))) & (kPenQueue - 1)] =
-                                make_float4(dx, dy, g, m);
-                        qt += __popc(bal);
-                        if (qt - qh >= 32) {  // at most 63 queued: the ring never overflows
-                            __syncwarp();
-                            pen_scatter<NE>(cs, w, n, my, q[(qh + lane) & (kPenQueue - 1)]);
-                            qh += 32;
-                            __syncwarp();  // drained slots are refilled next
-                        }
-                    }
+
+    // one (pose, point) pair; every thread of the block calls this the same
+    // number of times, so that the whole warp takes part in every ballot
+    auto pair = [&](float2 pt, bool valid) __attribute__((always_inline)) {
+        const float dx = pt.x - ftx, dy = pt.y - fty;
+        const float m = margin_of<NE>(cs, w, n, dx, dy);
+        const float z = -m * inv_tau;
+        const float e = exp_neg_abs(z);
+        if (!BACKWARD) {
+            if (valid) l_acc += fmaxf(z, 0.f) + log1p_small(e);  // softplus(z)
+        } else {
+            const float g = -sigmoid_from(z, e) * inv_tau;  // dL/dm
+            const bool hot = valid && g != 0.f;
+            const unsigned bal = __ballot_sync(0xffffffffu, hot);
+            if (bal) {
+                if (hot)
+                    q[(qt + __popc(bal & ((1u << lane) - 1u))) & (kPenQueue - 1)] = make_float4(dx, dy, g, m);
+                qt += __popc(bal);
+                if (qt - qh >= 32) {  // at most 63 queued: the ring never overflows
+                    __syncwarp();
+                    pen_scatter<NE>(cs, w, n, my, q[(qh + lane) & (kPenQueue - 1)]);
+                    qh += 32;
+                    __syncwarp();  // drained slots are refilled next
                 }
             }
         }
+    };
+    // Steps of kStep points, kPenUnroll per thread, with the next step's
+    // points loaded into the other register set while these are evaluated.
+    // FULL: a whole tile of kPenPoints, no bounds checks.
+    auto tile = [&](auto full) {
+        constexpr bool FULL = decltype(full)::value;
+        const int steps = FULL ? kPenPoints / kStep : (cnt + kStep - 1) / kStep;
+        auto load = [&](int st, float2 (&p)[kPenUnroll]) {
+#pragma unroll
+            for (int u = 0; u < kPenUnroll; ++u) {
+                const int i = st * kStep + u * kPenThreads + (int)threadIdx.x;
+                p[u] = (FULL || i < cnt) ? bp[i] : make_float2(ftx, fty);
+            }
+        };
+        auto eval = [&](int st, const float2 (&p)[kPenUnroll]) {
+#pragma unroll
+            for (int u = 0; u < kPenUnroll; ++u)
+                pair(p[u], FULL || st * kStep + u * kPenThreads + (int)threadIdx.x < cnt);
+        };
+        float2 a[kPenUnroll], b[kPenUnroll];
+        load(0, a);
+        for (int st = 0; st < steps; st += 2) {
+            if (FULL || st + 1 < steps) load(st + 1, b);
+            eval(st, a);
+            if (st + 2 < steps) load(st + 2, a);
+            if (FULL || st + 1 < steps) eval(st + 1, b);
+        }
+    };
+    static_assert(kPenPoints % (2 * kStep) == 0, "a full tile is an even number of steps");
+    if (n > 0) {
+        if (cnt == kPenPoints) tile(BoolTag<true>());
+        else tile(BoolTag<false>());
         if (BACKWARD) {
             __syncwarp();
             if (lane < qt - qh) pen_scatter<NE>(cs, w, n, my, q[(qh + lane) & (kPenQueue - 1)]);
         }
     }
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t nb = (size_t)gridDim.x * gridDim.y;  // blocks of the launch
     if (!BACKWARD) {
         const double s = block_sum((double)l_acc, red);
         if (threadIdx.x == 0) loss_part[blk] = s;
@@ -341,128 +364,116 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
         // lane then a shuffle tree (float32, fixed order)
         __shared__ double es[kMaxEdges][3];
         const int wid = threadIdx.x >> 5;
-        for (int v = wid; v < 3 * kMaxEdges; v += kWarps) {
+        for (int v = wid; v < 3 * n; v += kWarps) {
             float t = 0.f;
-            if (v < 3 * n)
-                for (int r = lane; r < acc_rows<NE>(); r += 32) t += lane_acc[(size_t)r * kLW + v];
+            for (int r = lane; r < acc_rows<NE>(); r += 32) t += lane_acc[(size_t)r * kLW + v];
             for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             if (lane == 0) es[v / 3][v % 3] = (double)t;
         }
         __syncthreads();
         __shared__ double pg[kMaxEdges][3];
         const int k = threadIdx.x;
-        const double2 rc = pose_rot[pose];
-        if (k < kMaxEdges) {
+        if (k < n) {
             const double S = es[k][0], Dx = es[k][1], Dy = es[k][2];
-            const float4 c = k < n ? cs[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 c = cs[k];
             // dm/dt = -w',  dm/dtheta = (p - t) x w' = dy w'_x - dx w'_y
             pg[k][0] = -S * c.x;
             pg[k][1] = -S * c.y;
             pg[k][2] = Dy * c.x - Dx * c.y;
-            if (k < nv) {
-                // body coordinates: xb = R^T (p - t); zeros for an invalid footprint
-                double *ep = edge_part + (size_t)blk * nv * 3 + 3 * k;
-                ep[0] = S;
-                ep[1] = rc.x * Dx + rc.y * Dy;
-                ep[2] = -rc.y * Dx + rc.x * Dy;
-            }
+            // body coordinates: xb = R^T (p - t)
+            const double2 rc = pose_rot[pose];
+            edge_part[(size_t)(3 * k) * nb + blk] = S;
+            edge_part[(size_t)(3 * k + 1) * nb + blk] = rc.x * Dx + rc.y * Dy;
+            edge_part[(size_t)(3 * k + 2) * nb + blk] = -rc.y * Dx + rc.x * Dy;
+        } else if (k < nv) {
+            // an invalid footprint (n = 0): zeros
+            for (int c = 0; c < 3; ++c) edge_part[(size_t)(3 * k + c) * nb + blk] = 0.0;
         }
         __syncthreads();
         if (threadIdx.x < 3) {
             double v = 0.0;
             for (int e = 0; e < n; ++e) v += pg[e][threadIdx.x];  // fixed order
-            pose_part[3 * blk + threadIdx.x] = v;
+            pose_part[(size_t)threadIdx.x * nb + blk] = v;
         }
     }
 }
 
-// Fixed-order sums over the per-block slots.
-__global__ void penalty_loss_reduce(const double *__restrict__ part, int64_t blocks,
-                                    const float *__restrict__ grad_out, double *__restrict__ loss)
+// Fixed-order sums: block (b, r) adds row r's values [b L, (b + 1) L) of
+// part[r][count] (a strided pass, then a tree of fixed shape) into
+// out[r][gridDim.x].
+__global__ void __launch_bounds__(kPenThreads) penalty_sum_kernel(const double *__restrict__ part,
+                                                                  int64_t count, int64_t L,
+                                                                  double *__restrict__ out)
 {
     __shared__ double red[kPenThreads / 32];
+    const double *row = part + (size_t)blockIdx.y * count;
+    const int64_t lo = (int64_t)blockIdx.x * L, hi = min(lo + L, count);
     double s = 0.0;
-    for (int64_t b = threadIdx.x; b < blocks; b += blockDim.x) s += part[b];
+    for (int64_t b = lo + threadIdx.x; b < hi; b += kPenThreads) s += row[b];
     s = block_sum(s, red);
-    if (threadIdx.x == 0) *loss = s;
-    (void)grad_out;
-}
-
-// One block per reduced value, fixed order: values [0, 3n) are the edge sums
-// over every block; values [3n, 3n + 3P) are pose j's sums over its tiles.
-__global__ void __launch_bounds__(kPenThreads) penalty_backward_reduce(
-    const double *__restrict__ edge_part, const double *__restrict__ pose_part, int n, int P,
-    int64_t tiles, double *__restrict__ edge_sum, double *__restrict__ pose_sum)
-{
-    __shared__ double red[kPenThreads / 32];
-    const int v = blockIdx.x;
-    double s = 0.0;
-    if (v < 3 * n) {
-        const int64_t blocks = tiles * P;
-        for (int64_t b = threadIdx.x; b < blocks; b += blockDim.x) s += edge_part[(size_t)b * 3 * n + v];
-    } else {
-        const int j = (v - 3 * n) / 3, c = (v - 3 * n) % 3;
-        for (int64_t b = threadIdx.x; b < tiles; b += blockDim.x) s += pose_part[3 * ((int64_t)j * tiles + b) + c];
-    }
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) {
-        if (v < 3 * n) edge_sum[v] = s;
-        else pose_sum[v - 3 * n] = s;
-    }
+    if (threadIdx.x == 0) out[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
 // Backward chain rule in fp64: one block, one thread per edge (n <= 64).
-// Reduces the per-block slots, then
+// Adds the edge sums' first-level slots (fixed order), then
 //   per edge k (N = |x - p0|^2 - |x - p_k|^2 summed affinely, D = |p_k - p0|):
 //     dL/dp0  += -(X - S p0)/D + Nsum (p_k - p0) / (2 D^3)
 //     dL/dp_k  =  (X - S p_k)/D - Nsum (p_k - p0) / (2 D^3)
 //   then back through Eq. 8 (p_k = p0 - 2 L_k(p0) (a, b) / (a^2 + b^2)) and
 //   Eq. 3-4 (p0 = C / (3 S2)) to the vertices.  The pose gradients arrive
 //   summed per pose (dL/dt = -sum g R(theta) w, dL/dtheta = sum g (p - t) x
-//   R(theta) w, in world axes) and are only scaled here.
+//   R(theta) w, in world axes) and are only scaled here.  Edge k touches
+//   vertices v_{k-1} and v_k; each vertex adds its two edges' shares in a
+//   fixed order (no atomics).
 __global__ void __launch_bounds__(64) penalty_chain_kernel(
     const float *__restrict__ verts, int n, const double2 *__restrict__ g0tab,
     const double2 *__restrict__ gk, const PolyInfo *__restrict__ poly, const float *__restrict__ poses,
-    int P, const double *__restrict__ pose_sum, const double *__restrict__ edge_sum,
+    int P, const double *__restrict__ pose_sum, const double *__restrict__ edge_stage,
     const float *__restrict__ grad_out, double *__restrict__ grad_v, double *__restrict__ grad_pose)
 {
     __shared__ double sG0[2][64];
-    __shared__ double sgv[64][2];
+    __shared__ double sgen[64][4];  // edge k's share for (v_{k-1}.x, v_{k-1}.y, v_k.x, v_k.y)
+    __shared__ double scen[64][4];  // the same through the centroid
     const int k = threadIdx.x;
     const double scale = grad_out ? (double)grad_out[0] : 1.0;
     const bool ok = poly[0].status == PIP_OK;
     // pose gradients: one thread per pose, in a loop
-    for (int j = k; j < P; j += blockDim.x) {
-        grad_pose[3 * j] = ok ? scale * pose_sum[3 * j] : 0.0;
-        grad_pose[3 * j + 1] = ok ? scale * pose_sum[3 * j + 1] : 0.0;
-        grad_pose[3 * j + 2] = ok ? scale * pose_sum[3 * j + 2] : 0.0;
-    }
+    for (int j = k; j < P; j += blockDim.x)
+        for (int c = 0; c < 3; ++c) grad_pose[3 * j + c] = ok ? scale * pose_sum[(size_t)c * P + j] : 0.0;
     double G0x = 0.0, G0y = 0.0;
     double gxm = 0.0, gym = 0.0, gxk = 0.0, gyk = 0.0;  // this edge's share of the vertex gradient
     const int km = k == 0 ? n - 1 : k - 1;
+    double xm = 0.0, ym = 0.0, xk = 0.0, yk = 0.0;
     if (ok && k < n) {
-        const double S = edge_sum[3 * k], X = edge_sum[3 * k + 1], Y = edge_sum[3 * k + 2];
+        double E[3];
+        for (int c = 0; c < 3; ++c) {
+            double v = 0.0;
+            for (int b = 0; b < kEdgeChunks; ++b) v += edge_stage[(size_t)(3 * k + c) * kEdgeChunks + b];
+            E[c] = v;
+        }
+        const double S = E[0], X = E[1], Y = E[2];
         const double2 g0 = g0tab[0], g = gk[k];
         const double ux = g.x - g0.x, uy = g.y - g0.y;
         const double D = sqrt(ux * ux + uy * uy);
+        const double rD = 1.0 / D;
         const double Nsum = 2.0 * (X * ux + Y * uy) + S * (g0.x * g0.x + g0.y * g0.y - g.x * g.x - g.y * g.y);
-        const double D3 = 2.0 * D * D * D;
-        const double Gkx = (X - S * g.x) / D - Nsum * ux / D3;
-        const double Gky = (Y - S * g.y) / D - Nsum * uy / D3;
-        G0x = -(X - S * g0.x) / D + Nsum * ux / D3;
-        G0y = -(Y - S * g0.y) / D + Nsum * uy / D3;
+        const double h = 0.5 * Nsum * rD * rD * rD;  // Nsum / (2 D^3)
+        const double Gkx = (X - S * g.x) * rD - h * ux;
+        const double Gky = (Y - S * g.y) * rD - h * uy;
+        G0x = -(X - S * g0.x) * rD + h * ux;
+        G0y = -(Y - S * g0.y) * rD + h * uy;
         // Eq. 8 backward: a = y_k - y_{k-1}, b = x_{k-1} - x_k, c = x_k y_{k-1} - x_{k-1} y_k
-        const double xm = verts[2 * km], ym = verts[2 * km + 1], xk = verts[2 * k], yk = verts[2 * k + 1];
+        xm = verts[2 * km]; ym = verts[2 * km + 1]; xk = verts[2 * k]; yk = verts[2 * k + 1];
         const double a = yk - ym, b = xm - xk, c = xk * ym - xm * yk;
-        const double q = a * a + b * b;
+        const double rq = 1.0 / (a * a + b * b);
         const double L = a * g0.x + b * g0.y + c;
-        const double nG = a * Gkx + b * Gky;
-        G0x += Gkx - 2.0 * a * nG / q;
-        G0y += Gky - 2.0 * b * nG / q;
+        const double nG = (a * Gkx + b * Gky) * rq;  // (a Gkx + b Gky) / q
+        G0x += Gkx - 2.0 * a * nG;
+        G0y += Gky - 2.0 * b * nG;
         // d p_k / d(a, b, c), contracted with G_k
-        const double dA = -2.0 * (g0.x * nG / q + L * Gkx / q - 2.0 * a * L * nG / (q * q));
-        const double dB = -2.0 * (g0.y * nG / q + L * Gky / q - 2.0 * b * L * nG / (q * q));
-        const double dC = -2.0 * nG / q;
+        const double dA = -2.0 * (g0.x * nG + L * Gkx * rq - 2.0 * a * L * nG * rq);
+        const double dB = -2.0 * (g0.y * nG + L * Gky * rq - 2.0 * b * L * nG * rq);
+        const double dC = -2.0 * nG;
         // (a, b, c) as functions of v_{k-1} = (xm, ym) and v_k = (xk, yk)
         gxm = dB + dC * (-yk);
         gym = -dA + dC * xk;
@@ -471,16 +482,10 @@ __global__ void __launch_bounds__(64) penalty_chain_kernel(
     }
     sG0[0][k] = G0x;
     sG0[1][k] = G0y;
-    sgv[k][0] = 0.0;
-    sgv[k][1] = 0.0;
-    __syncthreads();
-    // the vertex gradient from the generators: edge k touches v_{k-1} and v_k
-    if (k < n) {
-        atomicAdd(&sgv[km][0], gxm);
-        atomicAdd(&sgv[km][1], gym);
-        atomicAdd(&sgv[k][0], gxk);
-        atomicAdd(&sgv[k][1], gyk);
-    }
+    sgen[k][0] = gxm;
+    sgen[k][1] = gym;
+    sgen[k][2] = gxk;
+    sgen[k][3] = gyk;
     __syncthreads();
     double Gx = 0.0, Gy = 0.0;
     for (int i = 0; i < n; ++i) {  // same order in every thread
@@ -488,6 +493,7 @@ __global__ void __launch_bounds__(64) penalty_chain_kernel(
         Gy += sG0[1][i];
     }
     // Eq. 3-4 backward: p0 = C / (3 S2), S2 = sum det_k, C = sum (v_{k-1} + v_k) det_k
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
     if (ok && k < n) {
         double S2 = 0.0;
         for (int i = 0; i < n; ++i) {
@@ -495,21 +501,29 @@ __global__ void __launch_bounds__(64) penalty_chain_kernel(
             S2 += (double)verts[2 * im] * verts[2 * i + 1] - (double)verts[2 * i] * verts[2 * im + 1];
         }
         const double2 g0 = g0tab[0];
-        const double lx = Gx / (3.0 * S2), ly = Gy / (3.0 * S2);
-        const double mu = -(Gx * g0.x + Gy * g0.y) / S2;
-        const double xm = verts[2 * km], ym = verts[2 * km + 1], xk = verts[2 * k], yk = verts[2 * k + 1];
+        const double rS = 1.0 / S2;
+        const double lx = Gx * rS * (1.0 / 3.0), ly = Gy * rS * (1.0 / 3.0);
+        const double mu = -(Gx * g0.x + Gy * g0.y) * rS;
         const double det = xm * yk - xk * ym;
         const double sx = xm + xk, sy = ym + yk;
         // d det / d(xm, ym, xk, yk) = (yk, -xk, -ym, xm)
-        atomicAdd(&sgv[km][0], lx * (det + sx * yk) + ly * (sy * yk) + mu * yk);
-        atomicAdd(&sgv[km][1], lx * (sx * -xk) + ly * (det + sy * -xk) + mu * -xk);
-        atomicAdd(&sgv[k][0], lx * (det + sx * -ym) + ly * (sy * -ym) + mu * -ym);
-        atomicAdd(&sgv[k][1], lx * (sx * xm) + ly * (det + sy * xm) + mu * xm);
+        c0 = lx * (det + sx * yk) + ly * (sy * yk) + mu * yk;
+        c1 = lx * (sx * -xk) + ly * (det + sy * -xk) + mu * -xk;
+        c2 = lx * (det + sx * -ym) + ly * (sy * -ym) + mu * -ym;
+        c3 = lx * (sx * xm) + ly * (det + sy * xm) + mu * xm;
     }
+    scen[k][0] = c0;
+    scen[k][1] = c1;
+    scen[k][2] = c2;
+    scen[k][3] = c3;
     __syncthreads();
     if (k < n) {
-        grad_v[2 * k] = ok ? scale * sgv[k][0] : 0.0;
-        grad_v[2 * k + 1] = ok ? scale * sgv[k][1] : 0.0;
+        // v_k ends edge k and starts edge k + 1
+        const int kp = k == n - 1 ? 0 : k + 1;
+        const double vx = (sgen[k][2] + sgen[kp][0]) + (scen[k][2] + scen[kp][0]);
+        const double vy = (sgen[k][3] + sgen[kp][1]) + (scen[k][3] + scen[kp][1]);
+        grad_v[2 * k] = ok ? scale * vx : 0.0;
+        grad_v[2 * k + 1] = ok ? scale * vy : 0.0;
     }
 }
 
@@ -578,7 +592,10 @@ pip_status pip_penalty_forward(const float *d_vertices, int32_t num_vertices, co
                                     w.coefn, w.poly, w.worst);
     launch_penalty<false>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses, d_points,
                           num_points, tau);
-    penalty_loss_reduce<<<1, kPenThreads, 0, s>>>(w.loss_part, tiles * num_poses, nullptr, d_loss);
+    const int64_t blocks = tiles * num_poses;
+    const int64_t g = (blocks + kRedPer - 1) / kRedPer;
+    penalty_sum_kernel<<<(unsigned)g, kPenThreads, 0, s>>>(w.loss_part, blocks, kRedPer, w.loss_stage);
+    penalty_sum_kernel<<<1, kPenThreads, 0, s>>>(w.loss_stage, g, g, d_loss);
     return cudaGetLastError() == cudaSuccess ? PIP_OK : PIP_E_CUDA;
 }
 
@@ -600,10 +617,14 @@ pip_status pip_penalty_backward(const float *d_vertices, int32_t num_vertices, c
                                     w.coefn, w.poly, w.worst);
     launch_penalty<true>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses, d_points,
                          num_points, tau);
-    penalty_backward_reduce<<<3 * num_vertices + 3 * num_poses, kPenThreads, 0, s>>>(
-        w.edge_part, w.pose_part, num_vertices, num_poses, tiles, w.edge_sum, w.pose_sum);
+    const int64_t blocks = tiles * num_poses;
+    // edge sums: kEdgeChunks slices per (edge, component); pose sums: one
+    // block per (pose, component) over the pose's tiles
+    penalty_sum_kernel<<<dim3(kEdgeChunks, 3 * num_vertices), kPenThreads, 0, s>>>(
+        w.edge_part, blocks, (blocks + kEdgeChunks - 1) / kEdgeChunks, w.edge_stage);
+    penalty_sum_kernel<<<dim3(num_poses, 3), kPenThreads, 0, s>>>(w.pose_part, blocks, tiles, w.pose_sum);
     penalty_chain_kernel<<<1, 64, 0, s>>>(d_vertices, num_vertices, w.g0, w.gk, w.poly, d_poses, num_poses,
-                                          w.pose_sum, w.edge_sum, d_grad_loss, d_grad_vertices,
+                                          w.pose_sum, w.edge_stage, d_grad_loss, d_grad_vertices,
                                           d_grad_poses);
     return cudaGetLastError() == cudaSuccess ? PIP_OK : PIP_E_CUDA;
 }

@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(
     if (!range_ok || n < kMinEdges || n > kMaxEdges) status = PIP_E_INVALID_ARG;
 
     double sx = 0.0, sy = 0.0;  // shift origin: vertex 0
-    double S = 0.0, Cx = 0.0, Cy = 0.0, turn = 0.0, D = 0.0;
+    double S = 0.0, Cx = 0.0, Cy = 0.0, D = 0.0;
+    int wraps[2] = {0, 0};  // vertices where the edge direction turns across angle 0, ccw / cw
     float bb[4] = {INFINITY, INFINITY, -INFINITY, -INFINITY};
     bool nonfinite = false, zero_edge = false, int_bad = false, fold = false;
     bool pos = false, neg = false;
@@ -93,19 +94,29 @@ __global__ void __launch_bounds__(256) prepare_kernel(
             Cx += (uxm + uxk) * det;
             Cy += (uym + uyk) * det;
             D = fmax(D, fmax(fabs(uxk), fabs(uyk)));
-            // turn at vertex k (exact sign), exterior angle for the winding number
+            // turn at vertex k (exact sign)
             const int o = orient_sign_exact(xm, ym, xk, yk, xp, yp);
             pos |= o > 0;
             neg |= o < 0;
             const double ex = xk - xm, ey = yk - ym, fx = xp - xk, fy = yp - yk;
             const double dt = ex * fx + ey * fy;
             if (o == 0 && !(dt > 0.0)) fold = true;
-            turn += atan2(ex * fy - ey * fx, dt);
+            // Winding of the edge direction: with every turn the same way
+            // (each less than pi), the direction crosses angle 0 once per full
+            // revolution, at the vertex where it passes from the lower
+            // half-plane of directions [-pi, 0) to the upper one [0, pi)
+            // (ccw) or back (cw).  Decided by comparisons of the coordinates
+            // alone, so exact.
+            const bool up_in = yk > ym || (yk == ym && xk > xm);
+            const bool up_out = yp > yk || (yp == yk && xp > xk);
+            wraps[0] += !up_in && up_out;
+            wraps[1] += up_in && !up_out;
         }
         S = warp_sum(S);
         Cx = warp_sum(Cx);
         Cy = warp_sum(Cy);
-        turn = warp_sum(turn);
+        wraps[0] = __reduce_add_sync(0xffffffffu, wraps[0]);
+        wraps[1] = __reduce_add_sync(0xffffffffu, wraps[1]);
         D = warp_max(D);
         nonfinite = __any_sync(0xffffffffu, nonfinite);
         int_bad = __any_sync(0xffffffffu, int_bad);
@@ -123,7 +134,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(
         else if (zero_edge) status = PIP_E_DEGENERATE;
         else if (!pos && !neg) status = PIP_E_DEGENERATE;           // all collinear: zero area
         else if ((pos && neg) || fold) status = PIP_E_NONCONVEX;
-        else if (fabs(turn) > 3.0 * M_PI) status = PIP_E_NONCONVEX;  // winds twice or more
+        else if (wraps[pos ? 0 : 1] != 1) status = PIP_E_NONCONVEX;  // winds twice or more
         else if (!(S * (pos ? 1.0 : -1.0) > 0.0)) status = PIP_E_DEGENERATE;
     }
 
