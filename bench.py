@@ -631,7 +631,15 @@ def run_other(args):
             cms = time_steps(cull, args.steps, 3, stream)
             extra["culled"] = {"ms_per_step": cms, "effective_Gtests_per_s": tests / (cms * 1e-3) / 1e9,
                                "note": "PIP_CULL: polygons skipped per warp by bounding box, early stop"}
-        launches = 3 if po is not None else (1 if (len(w.vertex_offsets) == 2 and p.data_ptr() % 16 == 0) else 2)
+        # our kernels per call: batch = items prefix, item fill, bulk, refine;
+        # all pairs = bulk, finalize, refine; one polygon = the pipelined
+        # kernel (refine inline), or bulk + refine for unaligned points
+        if po is not None:
+            launches = 4
+        elif len(w.vertex_offsets) > 2:
+            launches = 3
+        else:
+            launches = 1 if p.data_ptr() % 16 == 0 else 2
         t.close()
     clk = clocks.stop()
     value = tests / (ms * 1e-3) / 1e9

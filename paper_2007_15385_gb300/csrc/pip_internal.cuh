@@ -175,22 +175,29 @@ __device__ __forceinline__ void x_two_diff(double a, double b, double &d, double
     x_two_sum(a, -b, d, e);
 }
 
-// Adds v to the expansion h[0..len) (nonoverlapping, increasing magnitude).
+// Adds v to the expansion h[0..len) (nonoverlapping, increasing magnitude),
+// dropping zero components as it goes (the same paper's zero elimination), so
+// that the expansion stays as short as the value needs: when the coordinate
+// differences are exact (their tails zero), the determinant is two exact
+// products and the expansion holds at most four terms.
 __device__ __forceinline__ int x_grow(double *h, int len, double v)
 {
+    if (v == 0.0) return len;
     double q = v;
+    int out = 0;
     for (int i = 0; i < len; ++i) {
         double s, e;
         x_two_sum(q, h[i], s, e);
-        h[i] = e;
+        if (e != 0.0) h[out++] = e;
         q = s;
     }
-    h[len] = q;
-    return len + 1;
+    if (q != 0.0) h[out++] = q;
+    return out;
 }
 
 __device__ __forceinline__ int x_add_product(double *h, int len, double a, double b, bool neg)
 {
+    if (a == 0.0 || b == 0.0) return len;
     double p = __dmul_rn(a, b);
     double e = __fma_rn(a, b, -p);
     if (neg) { p = -p; e = -e; }
@@ -230,9 +237,8 @@ static __device__ __noinline__ int orient_sign_exact(double ax, double ay, doubl
     len = x_add_product(h, len, w1, z0, true);
     len = x_add_product(h, len, w0, z1, true);
     len = x_add_product(h, len, w0, z0, true);
-    for (int i = len - 1; i >= 0; --i)
-        if (h[i] != 0.0) return h[i] > 0.0 ? 1 : -1;
-    return 0;
+    // zero-free and ordered by magnitude: the last term carries the sign
+    return len == 0 ? 0 : (h[len - 1] > 0.0 ? 1 : -1);
 }
 
 }  // namespace pip

@@ -56,13 +56,14 @@ struct RaggedCfg {
     static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
 };
 
-// Single block.  Items of polygon j are the chunks of the kTile grid its
-// range [poffs[j], poffs[j+1]) touches.  Bad offsets (not a non-decreasing
-// cover of [0, M)) leave zero items and raise PIP_E_INVALID_ARG in *worst.
+// Single block: the offsets' check and the exclusive prefix of the items per
+// polygon.  Items of polygon j are the chunks of the kTile grid its range
+// [poffs[j], poffs[j+1]) touches.  Bad offsets (not a non-decreasing cover of
+// [0, M)), or more items than the table holds, leave a total prefix[P] of zero
+// and raise PIP_E_INVALID_ARG in *worst.
 __global__ void __launch_bounds__(1024) ragged_items_kernel(
-    const int64_t *__restrict__ poffs, int P, int64_t M, int tile, int64_t *__restrict__ prefix,
-    RaggedItem *__restrict__ items, int64_t cap, unsigned int *__restrict__ counters,
-    unsigned int *__restrict__ qcount, int32_t *__restrict__ worst, uint32_t *__restrict__ mask)
+    const int64_t *__restrict__ poffs, int P, int64_t M, int tile, int64_t *__restrict__ prefix, int64_t cap,
+    unsigned int *__restrict__ counters, unsigned int *__restrict__ qcount, int32_t *__restrict__ worst)
 {
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t carry;
@@ -110,21 +111,35 @@ __global__ void __launch_bounds__(1024) ragged_items_kernel(
         prefix[P] = ok ? carry : 0;
         if (!ok) atomicMax(worst, (int)PIP_E_INVALID_ARG);
     }
-    if (!ok) return;
-    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+}
+
+// One warp per polygon, many blocks: the polygon's items (lane-strided), and
+// zeros in the mask words it shares with its neighbours (they are OR-ed into
+// later).  Nothing when the prefix pass found the offsets bad (total zero).
+__global__ void __launch_bounds__(256) ragged_fill_kernel(const int64_t *__restrict__ poffs, int P, int tile,
+                                                          const int64_t *__restrict__ prefix,
+                                                          RaggedItem *__restrict__ items,
+                                                          uint32_t *__restrict__ mask)
+{
+    const int64_t total = prefix[P];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < P; j += nwarps) {
         const int64_t a = poffs[j], b = poffs[j + 1];
         if (b <= a) continue;
-        if (a & 31) mask[a >> 5] = 0u;
-        if (b & 31) mask[(b - 1) >> 5] = 0u;
-        int64_t i = prefix[j];
-        for (int64_t k = a / tile; k * tile < b; ++k, ++i) {
-            const int64_t c0 = k * tile;
+        const int64_t k0 = a / tile, nk = (b - 1) / tile - k0 + 1;
+        const int64_t i0 = prefix[j];
+        if (i0 < 0 || i0 + nk > total) continue;
+        if (lane == 0 && (a & 31)) mask[a >> 5] = 0u;
+        if (lane == 1 && (b & 31)) mask[(b - 1) >> 5] = 0u;
+        for (int64_t r = lane; r < nk; r += 32) {
+            const int64_t c0 = (k0 + r) * tile;
             RaggedItem it;
             it.j = j;
-            it.k = (int32_t)k;
+            it.k = (int32_t)(k0 + r);
             it.lo = (int32_t)(max(a, c0) - c0);
             it.hi = (int32_t)(min(b, c0 + tile) - c0);
-            items[i] = it;
+            items[i0 + r] = it;
         }
     }
 }

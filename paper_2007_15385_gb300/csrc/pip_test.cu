@@ -68,8 +68,10 @@ cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t 
                                   uint32_t *mask, cudaStream_t s)
 {
     using C = RaggedCfg<PPL, STAGES>;
-    ragged_items_kernel<<<1, 1024, 0, s>>>(poffs, t->P, M, C::kTile, t->d_items, (RaggedItem *)t->d_ritems,
-                                           t->ritems_cap, t->d_work, t->d_qcount, t->d_worst, mask);
+    ragged_items_kernel<<<1, 1024, 0, s>>>(poffs, t->P, M, C::kTile, t->d_items, t->ritems_cap, t->d_work,
+                                           t->d_qcount, t->d_worst);
+    ragged_fill_kernel<<<(unsigned)std::min((t->P + 7) / 8, t->num_sms * 8), 256, 0, s>>>(
+        poffs, t->P, C::kTile, t->d_items, (RaggedItem *)t->d_ritems, mask);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto k = ragged_tma_kernel<PPL, STAGES, INT>;
