@@ -90,6 +90,7 @@ struct pip_tables {
     float4 *d_coef;
     float4 *d_coefn;
     float4 *d_coefp;             // [P][kPadStride] coefficients padded per polygon (all pairs, batch)
+    int4 *d_iedge;               // [V] integer polygons: (v_{k-1}, oriented edge k); null for float ones
     pip::PolyInfo *d_poly;
     uint32_t *d_queue;
     uint32_t *d_keys;            // [max_points] all-pairs candidate keys

@@ -36,6 +36,7 @@ struct NoAllocScratch {
     double2 gk[kMaxEdges];
     float4 coef[kMaxEdges];
     float4 coefn[kMaxEdges];
+    int4 iedge[kMaxEdges];
     uint32_t queue[kNoAllocMaxPoints];
 };
 
@@ -108,6 +109,7 @@ extern "C" pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype 
     noalloc_begin_kernel<<<1, 32, 0, cs>>>(s, num_vertices);
     prepare_kernel<<<1, 32, 0, cs>>>(d_vertices, vdtype, s->voffs, 1, num_vertices, &s->g0, s->gk,
                                      s->coef, s->coefn, &s->poly, &s->worst);
+    if (vdtype == PIP_I32) int_edge_kernel<<<1, 32, 0, cs>>>(&s->poly, (const int2 *)d_vertices, 1, s->iedge);
     PIP_CUDA_TRY(cudaGetLastError());
     if (d_status != nullptr)
         PIP_CUDA_TRY(cudaMemcpyAsync(d_status, &s->worst, sizeof(int32_t), cudaMemcpyDeviceToDevice, cs));
@@ -144,6 +146,7 @@ extern "C" pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype 
     A.qcount = &s->qcount;
     A.mask = d_mask;
     A.first_hit = nullptr;
+    A.iedge = s->iedge;
     refine_kernel<false><<<num_sms * 2, kThreads, 0, cs>>>(A, kSingle);
     PIP_CUDA_TRY(cudaGetLastError());
     return PIP_OK;

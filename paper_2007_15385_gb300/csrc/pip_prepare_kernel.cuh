@@ -261,4 +261,24 @@ __global__ void __launch_bounds__(256) prepare_kernel(
     }
 }
 
+// Integer polygons, for the exact refine: per edge k the start vertex
+// v_{k-1} and the edge vector oriented by the polygon's turn, e_k = orient
+// (v_k - v_{k-1}), so that p is inside (closed) iff cross(e_k, p - v_{k-1}) >= 0
+// for every k.  |v| <= 2^24 keeps e_k in int32.  One warp per polygon;
+// invalid polygons get nothing (the refine reads their status first).
+__global__ void int_edge_kernel(const PolyInfo *__restrict__ poly, const int2 *__restrict__ verts, int P,
+                                int4 *__restrict__ iedge)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    if (j >= P) return;
+    const PolyInfo pi = poly[j];
+    if (pi.status != PIP_OK) return;
+    for (int k = lane; k < pi.n; k += 32) {
+        const int km = k == 0 ? pi.n - 1 : k - 1;
+        const int2 a = verts[pi.voff + km], b = verts[pi.voff + k];
+        iedge[pi.voff + k] = make_int4(a.x, a.y, pi.orient * (b.x - a.x), pi.orient * (b.y - a.y));
+    }
+}
+
 }  // namespace

@@ -531,6 +531,7 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     A.mask = mask;
     A.first_hit = hit;
     A.keys = t->d_keys;
+    A.iedge = t->d_iedge;
     // the pipelined batch kernel files the polygon of each queued point in the keys buffer
     A.qpoly = (kmode == kRagged && v16) ? t->d_keys : nullptr;
     if (kmode != kAllPairs && t->vdtype == PIP_I32 && pdtype == PIP_I32)

@@ -291,6 +291,7 @@ struct RefineArgs {
     int32_t *first_hit;
     const uint32_t *keys;  // all-pairs candidate keys (pip_test's split path)
     const uint32_t *qpoly; // own-polygon batch: the polygon of each queued point, or null
+    const int4 *iedge;     // integer polygons: (v_{k-1}, oriented edge k) per edge
 };
 
 __device__ __forceinline__ void vertex_d(const void *verts, int vdtype, int64_t i, double &x, double &y)
@@ -308,30 +309,25 @@ __device__ __forceinline__ void vertex_d(const void *verts, int vdtype, int64_t 
 
 // Integer polygon and point: every edge's orientation in int64 (exact),
 // the point inside iff none has the opposite sign of the polygon's turn.
-__device__ __forceinline__ bool inside_exact_int(const RefineArgs &A, int n, int v0, int sigma, int64_t i)
+__device__ __forceinline__ bool inside_exact_int(const RefineArgs &A, int n, int v0, int64_t i)
 {
     const int2 pq = ((const int2 *)A.pts)[i];
-    const int2 *v = (const int2 *)A.verts + v0;
-    int2 a = v[n - 1];
+    const int4 *e = A.iedge + v0;  // (a, oriented edge): inside iff every cross >= 0
     // -2^30 <= p < 2^30 per coordinate (unsigned compare: no abs overflow at INT_MIN)
     if ((uint32_t)pq.x + (1u << 30) < (1u << 31) && (uint32_t)pq.y + (1u << 30) < (1u << 31)) {
-        // |v| <= 2^24: every difference fits in int32, each product is one
-        // 32 x 32 -> 64-bit multiply (|product| < 2^56), the cross product exact
+        // |e| <= 2^25 and |p - a| < 2^31: each product is one 32 x 32 -> 64-bit
+        // multiply (|product| < 2^56), the cross product exact
         for (int k = 0; k < n; ++k) {
-            const int2 b = v[k];
-            const int64_t cr = (int64_t)(b.x - a.x) * (pq.y - a.y) - (int64_t)(b.y - a.y) * (pq.x - a.x);
-            if ((cr > 0 ? 1 : (cr < 0 ? -1 : 0)) == -sigma) return false;
-            a = b;
+            const int4 E = e[k];
+            if ((int64_t)E.z * (pq.y - E.y) - (int64_t)E.w * (pq.x - E.x) < 0) return false;
         }
         return true;
     }
     const int64_t px = pq.x, py = pq.y;
     for (int k = 0; k < n; ++k) {
-        const int2 b = v[k];
-        // |b - a| <= 2^25 and |p - a| < 2^32 + 2^24: each product < 2^58
-        const int64_t cr = (int64_t)(b.x - (int64_t)a.x) * (py - a.y) - (int64_t)(b.y - (int64_t)a.y) * (px - a.x);
-        if ((cr > 0 ? 1 : (cr < 0 ? -1 : 0)) == -sigma) return false;
-        a = b;
+        const int4 E = e[k];
+        // |p - a| < 2^32 + 2^24: each product < 2^58
+        if ((int64_t)E.z * (py - E.y) - (int64_t)E.w * (px - E.x) < 0) return false;
     }
     return true;
 }
@@ -344,7 +340,7 @@ __device__ bool inside_exact(const RefineArgs &A, int j, int64_t i)
     const PolyInfo pi = A.poly[j];
     if (pi.status != PIP_OK) return false;
     const int n = pi.n, v0 = pi.voff, sigma = pi.orient;
-    if (A.vdtype == PIP_I32 && A.pdtype == PIP_I32) return inside_exact_int(A, n, v0, sigma, i);
+    if (A.vdtype == PIP_I32 && A.pdtype == PIP_I32) return inside_exact_int(A, n, v0, i);
     double px, py;
     vertex_d(A.pts, A.pdtype, i, px, py);
     if (!isfinite(px) || !isfinite(py)) return false;
@@ -416,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) refine_kernel(RefineArgs A, int mode
         bool in;
         if (INT) {
             const PolyInfo *pi = A.poly + j;
-            in = pi->status == PIP_OK && inside_exact_int(A, pi->n, pi->voff, pi->orient, i);
+            in = pi->status == PIP_OK && inside_exact_int(A, pi->n, pi->voff, i);
         } else {
             in = inside_exact(A, j, i);
         }
