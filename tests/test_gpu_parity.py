@@ -143,6 +143,20 @@ def test_gis_batch_with_empty_and_tiny_polygons():
     assert_same(got, oracle_own(w), "gis tiny")
 
 
+@pytest.mark.parametrize("ints", [False, True])
+def test_batch_with_more_polygons_than_one_pass_of_the_setup_kernels(ints):
+    """12,000 polygons: the one-block item prefix takes 12 passes of 1,024
+    polygons, and the item fill (one warp per polygon, at most 8 blocks of 8
+    warps per SM) loops over the polygons."""
+    if ints:
+        w = wl.integer_hulls(seed=62, num_polygons=12000, points_per_polygon=24)
+    else:
+        w = wl.gis_batch(seed=61, num_polygons=12000, m_range=(0, 40))
+    got, _, _, st = run_test(w)
+    assert st == B.PIP_OK
+    assert_same(got, oracle_own(w), "12,000 polygons")
+
+
 def test_gis_batch_unaligned_points():
     # points 8 bytes past a 16-byte boundary: the batch runs without bulk copies
     w = wl.gis_batch(seed=17, num_polygons=48, m_range=(10, 3000))
