@@ -391,6 +391,15 @@ def main():
             cms = c0.elapsed_time(c1) / reps
             comparators[name] = {"ms": cms, "Gtests_per_s": tests_per_step / (cms * 1e-3) / 1e9}
 
+    # the signed margin (pip_margin) on the same points, apart from the step:
+    # 8 B read + 4 B written per point, against the same HBM peak
+    marg = torch.empty(M, dtype=torch.float32, device=dev)
+    mms = time_steps(lambda: B.pip_margin(t, p, out=marg), 20, 3, stream)
+    margin = {"ms": mms, "Gtests_per_s": tests_per_step / (mms * 1e-3) / 1e9,
+              "achieved": M * 12 / (mms * 1e-3) / 1e9, "unit": "GB/s", "peak": peak,
+              "frac": M * 12 / (mms * 1e-3) / 1e9 / peak, "bytes_per_point": 12}
+    del marg
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_run(w, 1 << 25)
@@ -419,6 +428,7 @@ def main():
                          "bytes_per_launch": bytes_per_launch, "kernel_ms": bulk_avg_ms,
                          "refine_kernel_ms": refine_ms / max(1, calls)},
             "comparators": comparators,
+            "margin": margin,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
