@@ -8,6 +8,7 @@
 // so the inner loop is the same two FMAs and a min as the inclusion test.
 // A point with a non-finite coordinate gets +inf (outside).
 #include "pip_kernels.cuh"
+#include "pip_margin_tma.cuh"
 
 using namespace pip;
 
@@ -208,6 +209,10 @@ extern "C" pip_status pip_margin(const pip_tables *t, const void *d_points, pip_
         if (ints) { if (v16) LAUNCH_MR(true, true) else LAUNCH_MR(true, false) }
         else { if (v16) LAUNCH_MR(false, true) else LAUNCH_MR(false, false) }
 #undef LAUNCH_MR
+    } else if (t->P == 1 && v16) {
+        // 16-byte aligned points: the pipelined kernel (bulk copies through shared memory)
+        PIP_CUDA_TRY(ints ? launch_margin_tma<true>(t, d_points, M, d_margin, s)
+                          : launch_margin_tma<false>(t, d_points, M, d_margin, s));
     } else if (t->P == 1) {
         const int64_t chunks = (M + Chunk<kF>::kPoints - 1) / Chunk<kF>::kPoints;
 #define LAUNCH_MS(I, V)                                                                              \

@@ -536,6 +536,36 @@ def test_margin_matches_oracle():
     t.close()
 
 
+@pytest.mark.parametrize("ints", [False, True])
+def test_margin_pipelined_equals_register_streaming(ints):
+    """16-byte aligned points take the pipelined margin kernel, points 8 bytes
+    past a boundary the register-streaming one; both evaluate the same float32
+    terms in the same order, so the margins are identical, and within the
+    float32 bound of the oracle.  70,001 points: 18 tiles and an odd last
+    point outside the bulk copies."""
+    if ints:
+        h = wl.integer_hulls(seed=63, num_polygons=1, points_per_polygon=70_001)
+        verts, pts = h.vertices, h.points
+    else:
+        w = wl.vehicle_footprint(m=70_001, seed=64)
+        verts, pts = w.vertices, w.points
+    M = len(pts)
+    t = B.pip_prepare(torch.from_numpy(verts).to(dev()), torch.tensor([0, len(verts)], dtype=torch.int32,
+                                                                      device=dev()), max_points=M)
+    flat = torch.from_numpy(np.ascontiguousarray(pts).reshape(-1)).to(dev())
+    shifted = torch.zeros(2 * M + 2, dtype=flat.dtype, device=dev())
+    shifted[2:] = flat
+    assert flat.data_ptr() % 16 == 0 and shifted[2:].data_ptr() % 16 == 8
+    a = B.pip_margin(t, flat).cpu().numpy()
+    b = B.pip_margin(t, shifted[2:]).cpu().numpy()
+    np.testing.assert_array_equal(a.view(np.uint32), b.view(np.uint32))
+    want = oracle.margin(verts, pts)
+    # float32 terms relative to o: a few ulps of |x| and of the edge offsets
+    tol = 16 * 2 ** -24 * (np.abs(np.asarray(pts, np.float64)).max(axis=1) + 2 * np.abs(verts).max() + 4.0)
+    assert np.all(np.abs(a.astype(np.float64) - want) <= tol)
+    t.close()
+
+
 def test_margin_ragged_and_all_pairs():
     w = wl.gis_batch(seed=20, num_polygons=30, m_range=(10, 3000))
     v = torch.from_numpy(w.vertices).to(dev())
