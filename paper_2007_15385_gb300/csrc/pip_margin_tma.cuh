@@ -5,8 +5,9 @@
 // guarded by full / empty mbarriers, eight consumer warps taking one slice of
 // a stage each and writing one float per point.  The coefficients sit in
 // shared memory (one broadcast load per edge for 16 points a lane), so one
-// instantiation serves every edge count.  Same arithmetic, in the same order,
-// as the register-streaming margin kernel: the results are identical.
+// instantiation serves every edge count.  The same float32 terms as the
+// register-streaming margin kernel, and an exact min: the results are
+// identical.
 #pragma once
 
 #include "pip_kernels.cuh"
@@ -29,22 +30,24 @@ struct MarginCfg {
 };
 
 // One consumer warp, one slice of 32 * PPL points starting at wfirst; the
-// stage holds the points the bulk copy moved, and an odd last point of the
-// set (not in the copy) is read from global memory.
-template <int PPL, bool INT>
+// stage holds the points the bulk copy moved.  TAIL: the slice may run past
+// M, or hold an odd last point of the set (not in the copy, read from global
+// memory).  The min takes three operands at a time; min is exact, so the
+// result equals the two-operand chain of the register-streaming kernel.
+template <int PPL, bool INT, bool TAIL>
 __device__ __forceinline__ void margin_slice(const float4 *cs, int npad, float ox, float oy,
                                              const unsigned char *stage, const void *__restrict__ pts,
                                              int64_t M, int64_t wfirst, int lane, float *__restrict__ out)
 {
-    const int nvalid = (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst));
+    const int nvalid = TAIL ? (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst)) : 32 * PPL;
     float x[PPL], y[PPL], m[PPL];
     bool fin[PPL];
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
         const int r = 32 * q + lane;
         float px = 0.f, py = 0.f;
-        if (r < nvalid) {
-            if (wfirst + r == M - 1 && (M & 1)) {
+        if (!TAIL || r < nvalid) {
+            if (TAIL && wfirst + r == M - 1 && (M & 1)) {
                 if (INT) {
                     px = (float)((const int32_t *)pts)[2 * (M - 1)];
                     py = (float)((const int32_t *)pts)[2 * (M - 1) + 1];
@@ -68,17 +71,20 @@ __device__ __forceinline__ void margin_slice(const float4 *cs, int npad, float o
         m[q] = INFINITY;
     }
     for (int k = 0; k < npad; k += 4) {
+        const float4 c0 = cs[k], c1 = cs[k + 1], c2 = cs[k + 2], c3 = cs[k + 3];
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const float4 c = cs[k + kk];
-#pragma unroll
-            for (int q = 0; q < PPL; ++q) m[q] = fminf(m[q], fmaf(-x[q], c.x, fmaf(-y[q], c.y, c.z)));
+        for (int q = 0; q < PPL; ++q) {
+            const float s0 = fmaf(-x[q], c0.x, fmaf(-y[q], c0.y, c0.z));
+            const float s1 = fmaf(-x[q], c1.x, fmaf(-y[q], c1.y, c1.z));
+            const float s2 = fmaf(-x[q], c2.x, fmaf(-y[q], c2.y, c2.z));
+            const float s3 = fmaf(-x[q], c3.x, fmaf(-y[q], c3.y, c3.z));
+            m[q] = fmin3(fmin3(m[q], s0, s1), s2, s3);
         }
     }
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
         const int r = 32 * q + lane;
-        if (r < nvalid) out[wfirst + r] = fin[q] ? -m[q] : INFINITY;
+        if (!TAIL || r < nvalid) out[wfirst + r] = fin[q] ? -m[q] : INFINITY;
     }
 }
 
@@ -142,10 +148,15 @@ __global__ void __launch_bounds__(kMarginThreads, 2) margin_tma_kernel(const Pol
         int s = 0;
         uint32_t fphase = 0;
         int64_t wfirst = (int64_t)blockIdx.x * kTile + warp * 32 * PPL;
+        // slices that end before the last point (or at an even end) need no bounds logic
+        const int64_t whole_end = (M & 1) ? M - 1 : M;
         for (int64_t it = 0; it < mine; ++it, wfirst += step) {
             if (!mbar_wait(&full[s], fphase, err)) break;
             const unsigned char *stage = smem + (size_t)s * C::kStageBytes + (size_t)warp * 32 * PPL * 8;
-            margin_slice<PPL, INT>(cs, npad, pi.ox, pi.oy, stage, pts, M, wfirst, lane, out);
+            if (wfirst + 32 * PPL <= whole_end)
+                margin_slice<PPL, INT, false>(cs, npad, pi.ox, pi.oy, stage, pts, M, wfirst, lane, out);
+            else
+                margin_slice<PPL, INT, true>(cs, npad, pi.ox, pi.oy, stage, pts, M, wfirst, lane, out);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
             if (++s == STAGES) {
