@@ -4,9 +4,10 @@
 //
 // Schedule.  The point array is cut at a fixed grid of kTile-point chunks;
 // a work item is one polygon's points inside one chunk, {j, k, lo, hi}, the
-// points k*kTile + [lo, hi).  A single-block setup kernel validates the point
-// offsets, writes the item table (items of one polygon are consecutive) and
-// zeroes the mask words that straddle two polygons' ranges.
+// points k*kTile + [lo, hi).  A single-block kernel validates the point
+// offsets and forms the prefix of the items per polygon; a many-block kernel
+// (one warp per polygon) writes the item table (items of one polygon are
+// consecutive) and zeroes the mask words that straddle two polygons' ranges.
 //
 // Persistent CTAs, one producer warp and seven consumer warps (16 warps per SM
 // at two CTAs: 128 registers a thread, 16 points per lane).  The producer
