@@ -43,6 +43,8 @@ FALLBACK_HBM_GBS = 6800.0
 # of 2^25 points scaled by 2 to the 2^26-point launch,
 # valid only while the kernel sources hash to the value recorded with it.
 NCU_TRAFFIC = {"bytes": 548029440, "sources_sha": "b192a863611cdb65"}
+# GB300 HBM3e nominal bandwidth, reported beside the measured-peak fraction
+NOMINAL_HBM_GBS = 7900.0
 KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_stream_tma.cuh",
                   "paper_2007_15385_gb300/csrc/pip_tma.cuh",
                   "paper_2007_15385_gb300/csrc/pip_kernels.cuh",
@@ -423,6 +425,7 @@ def main():
             "gpu_launches": calls_launches * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "peak_kind": peak_kind + " hbm_gbs",
                          "kernel": "stream_tma_kernel (float32 test + inline exact refine)",
                          "bytes_per_launch": bytes_per_launch, "kernel_ms": bulk_avg_ms,
