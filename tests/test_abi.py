@@ -66,3 +66,38 @@ def test_host_argument_checks(lib):
 
 def test_build_flags_target_sm103a():
     assert "arch=compute_103a,code=sm_103a" in build_mod.ARCH
+
+
+def test_host_argument_checks_of_the_other_entry_points(lib):
+    """Every entry point refuses a null table handle or a bad size on the host,
+    before any device work; the size helpers compute their bytes on the host."""
+    i32, f64 = ctypes.c_int32(0), ctypes.c_double(0.0)
+    fms = ctypes.c_float(0.0)
+    assert lib.pip_timing(None, 1) == B.PIP_E_INVALID_ARG
+    assert lib.pip_timing_read(None, ctypes.byref(i32), ctypes.byref(f64), ctypes.byref(f64)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_get_polygon_status(None, None, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_export_tables(None, None, None, None, None, None, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_set_stream_variant(None, 0) == B.PIP_E_INVALID_ARG
+    assert lib.pip_set_batch_variant(None, 0) == B.PIP_E_INVALID_ARG
+    assert lib.pip_autotune_stream(None, None, 0, 1, None, 1, None, ctypes.byref(i32),
+                                   ctypes.byref(fms)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_autotune_batch(None, None, 0, 1, None, None, 1, None, ctypes.byref(i32),
+                                  ctypes.byref(fms)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_selftest_wait_timeout(None, None, 1000, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_rasterize(None, 8, 8, 0.0, 0.0, 1.0, 1.0, None, None, None, 0, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_stream_variant_count() >= 1 and lib.pip_batch_variant_count() >= 1
+    # raster workspace: one bit per (tile, polygon), tiles of 64 x 48 pixels
+    assert lib.pip_raster_workspace_bytes(0, 10, 10) == 0
+    assert lib.pip_raster_workspace_bytes(1, 0, 10) == 0
+    assert lib.pip_raster_workspace_bytes(33, 64, 48) == 2 * 4
+    assert lib.pip_raster_workspace_bytes(32, 65, 49) == 4 * 4
+    # penalty: bad sizes and null pointers are refused; the workspace size grows with the blocks
+    assert lib.pip_penalty_workspace_bytes(0, 1, 1) == 0
+    assert lib.pip_penalty_workspace_bytes(12, 4, 1 << 20) > lib.pip_penalty_workspace_bytes(12, 4, 1 << 10) > 0
+    assert lib.pip_penalty_forward(None, 12, None, 4, None, 10, 0.05, None, None, 0, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_penalty_backward(None, 12, None, 4, None, 10, 0.05, None, None, None, None, 0,
+                                    None) == B.PIP_E_INVALID_ARG
+    # the allocation-free one-polygon call checks its arguments first
+    assert lib.pip_test_single_noalloc(None, 0, 8, None, 0, 10, None, None, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_test_single_noalloc(8, 5, 8, 8, 0, 10, 8, None, None) == B.PIP_E_INVALID_ARG  # bad dtype
+    assert lib.pip_test_single_noalloc(8, 0, 2, 8, 0, 10, 8, None, None) == B.PIP_E_INVALID_ARG  # 2 vertices
