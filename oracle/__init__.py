@@ -24,6 +24,12 @@ inside_exact           Eq. 1 via the identity           exact-rational Alg. 5 br
                        |x-p_k|^2-|x-p_0|^2 =            points included), vertices/edge points in,
                        4 L_k(p_0) L_k(x)/(a^2+b^2)      bbox outside, area Monte Carlo, translation
                                                         and 90-degree rotation invariance
+inside_exact_ragged,   inside_exact per own polygon;    axis-aligned rectangles (both orientations)
+first_hit_exact        lowest polygon index holding     against plain coordinate comparisons,
+                       the point (closed)               lattice points on edges and corners;
+                                                        non-convex and zero-area polygons hold nothing
+raster_centres         pixel centres x0 + c dx,         exact rationals rounded once to float32
+                       one rounding (C fmaf)
 voronoi_fp64           Alg. 5 literally (fp64)          agreement with inside_exact off its own
                                                         ambiguity flag
 sign_of_offset         Alg. 2 literally (fp64)          agreement with inside_exact off-boundary

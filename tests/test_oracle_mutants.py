@@ -47,6 +47,9 @@ MUTANTS = {
                              "double gm = -sigmoid(best / tau) / tau;"),
     "raster_centre_two_roundings": ("= fmaf((float)c, dx, x0);", "= (float)c * dx + x0;"),
     "raster_row_spacing": ("fmaf((float)r, dy, y0);", "fmaf((float)r, dx, y0);"),
+    "first_hit_takes_the_last": ("if (in) { out[i] = j; break; }", "if (in) { out[i] = j; }"),
+    "ragged_drops_a_point": ("poffs[j + 1] - poffs[j], out + poffs[j]);",
+                             "poffs[j + 1] - poffs[j] - 1, out + poffs[j]);"),
 }
 
 

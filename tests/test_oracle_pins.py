@@ -567,3 +567,61 @@ def test_raster_centres_are_one_rounding_of_the_exact_grid():
         for r in range(H):
             want = _round_f32(Fraction(r) * Fraction(float(dy)) + Fraction(float(y0)))
             assert (got[r, :, 1] == want).all()
+
+
+def _rect(x0, y0, x1, y1, cw):
+    v = [[x0, y0], [x1, y0], [x1, y1], [x0, y1]]
+    return v[::-1] if cw else v
+
+
+def _in_rect(r, p):
+    """Closed membership of points p in an axis-aligned rectangle, by plain comparisons."""
+    (x0, y0, x1, y1) = r
+    return (p[:, 0] >= x0) & (p[:, 0] <= x1) & (p[:, 1] >= y0) & (p[:, 1] <= y1)
+
+
+def test_first_hit_and_ragged_on_rectangles_against_plain_comparisons():
+    """Axis-aligned rectangles (both orientations) hold a point iff its
+    coordinates lie within their bounds, closed; the first hit is the lowest
+    such index.  Coordinates on a 1/16 lattice put many points exactly on
+    edges and corners.  A non-convex and a zero-area polygon in the list hold
+    nothing."""
+    rng = np.random.default_rng(31)
+    rects, polys = [], []
+    for j in range(14):
+        x0, y0 = (rng.integers(0, 64, 2) / 8.0)
+        w, h = (rng.integers(1, 40, 2) / 8.0)
+        rects.append((x0, y0, x0 + w, y0 + h))
+        polys.append(_rect(x0, y0, x0 + w, y0 + h, cw=bool(j % 2)))
+    bad = [[[0, 0], [8, 0], [4, 1], [8, 8], [0, 8]],  # non-convex: holds nothing
+           [[0, 0], [4, 4], [8, 8]]]                   # zero area: holds nothing
+    polys = polys[:5] + bad + polys[5:]
+    rects = rects[:5] + [None, None] + rects[5:]
+    verts = np.concatenate([np.array(p, np.float32) for p in polys])
+    voffs = np.zeros(len(polys) + 1, np.int32)
+    voffs[1:] = np.cumsum([len(p) for p in polys])
+    pts = (rng.integers(-8, 13 * 16, size=(3000, 2)) / 16.0).astype(np.float32)
+    hit = oracle.first_hit_exact(verts, voffs, pts)
+    want = np.full(len(pts), -1)
+    for j in range(len(polys) - 1, -1, -1):  # lowest index wins
+        if rects[j] is not None:
+            want[_in_rect(rects[j], pts.astype(np.float64))] = j
+    np.testing.assert_array_equal(hit, want)
+    assert (want >= 0).sum() > 500 and (want == -1).sum() > 100
+    # ragged: each polygon against its own points, drawn on the 1/16 lattice
+    # of its rectangle widened by 1/8 (most inside, many on the boundary)
+    counts = rng.integers(0, 300, size=len(polys))
+    poffs = np.zeros(len(polys) + 1, np.int64)
+    poffs[1:] = np.cumsum(counts)
+    own = np.empty((int(poffs[-1]), 2), np.float32)
+    for j in range(len(polys)):
+        x0, y0, x1, y1 = rects[j] if rects[j] is not None else (0.0, 0.0, 8.0, 8.0)
+        ix = rng.integers(int(x0 * 16) - 2, int(x1 * 16) + 3, size=counts[j])
+        iy = rng.integers(int(y0 * 16) - 2, int(y1 * 16) + 3, size=counts[j])
+        own[poffs[j]:poffs[j + 1]] = np.stack([ix, iy], axis=1) / 16.0
+    got, _ = oracle.inside_exact_ragged(verts, voffs, own, poffs)
+    assert got.mean() > 0.5
+    for j in range(len(polys)):
+        sl = slice(poffs[j], poffs[j + 1])
+        exp = np.zeros(counts[j], bool) if rects[j] is None else _in_rect(rects[j], own[sl].astype(np.float64))
+        np.testing.assert_array_equal(got[sl].astype(bool), exp)
