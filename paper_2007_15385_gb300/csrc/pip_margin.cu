@@ -179,6 +179,18 @@ constexpr int kPT = 4;
 
 }  // namespace
 
+namespace pip {
+
+// Called by pip_prepare (outside any stream capture).
+cudaError_t margin_kernels_setup()
+{
+    cudaError_t e = setup_margin_tma<false>();
+    if (e == cudaSuccess) e = setup_margin_tma<true>();
+    return e;
+}
+
+}  // namespace pip
+
 extern "C" pip_status pip_margin(const pip_tables *t, const void *d_points, pip_dtype pdtype,
                                  int64_t num_points, const int64_t *d_point_offsets, float *d_margin,
                                  void *stream)

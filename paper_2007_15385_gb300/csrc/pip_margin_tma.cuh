@@ -167,16 +167,26 @@ __global__ void __launch_bounds__(kMarginThreads, 2) margin_tma_kernel(const Pol
     }
 }
 
+constexpr int kMarginPPL = 16, kMarginStages = 3;
+
+// Raises the kernel's dynamic shared-memory limit (once, from pip_prepare,
+// outside any stream capture).
+template <bool INT>
+cudaError_t setup_margin_tma()
+{
+    using C = MarginCfg<kMarginPPL, kMarginStages>;
+    return cudaFuncSetAttribute(margin_tma_kernel<kMarginPPL, kMarginStages, INT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
+}
+
 // Launches the pipelined margin over M points of the tables' one polygon
 // (16-byte aligned points).
 template <bool INT>
 cudaError_t launch_margin_tma(const pip_tables *t, const void *pts, int64_t M, float *out, cudaStream_t s)
 {
-    constexpr int kPPL = 16, kStages = 3;
+    constexpr int kPPL = kMarginPPL, kStages = kMarginStages;
     using C = MarginCfg<kPPL, kStages>;
     auto k = margin_tma_kernel<kPPL, kStages, INT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
-    if (e != cudaSuccess) return e;
     const int64_t tiles = (M + C::kTile - 1) / C::kTile;
     const int blocks = (int)max((int64_t)1, min((int64_t)2 * t->num_sms, tiles));
     k<<<blocks, kMarginThreads, C::kSmem, s>>>(t->d_poly, t->d_coefn, pts, M, out, t->d_error);

@@ -51,6 +51,9 @@ __global__ void pad_coef_kernel(const PolyInfo *__restrict__ poly, const float4 
 
 namespace pip {
 
+// pip_margin.cu: the pipelined margin kernel's shared-memory limit
+cudaError_t margin_kernels_setup();
+
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 pip_status check_tables(const pip_tables *t)
@@ -147,6 +150,7 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
         e = cudaMemcpyAsync(t->d_voffs, d_vertex_offsets, (P + 1) * 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt, 0, 128, s);
     if (e == cudaSuccess) e = stream_kernels_setup();
+    if (e == cudaSuccess) e = margin_kernels_setup();
     if (e == cudaSuccess) e = allpairs_setup();
     if (e == cudaSuccess) e = ragged_kernels_setup();
     if (e == cudaSuccess) {

@@ -671,6 +671,31 @@ def test_cuda_graph_capture_of_pip_test():
     t.close()
 
 
+def test_cuda_graph_capture_of_pip_margin():
+    """One polygon, aligned points: the pipelined margin kernel replayed from a
+    CUDA graph gives the eager call's margins exactly."""
+    w = wl.vehicle_footprint(m=20_001, seed=65)
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                      max_points=w.num_points)
+    p = torch.from_numpy(w.points).to(dev())
+    eager = B.pip_margin(t, p).cpu().numpy()
+    out = torch.zeros(w.num_points, dtype=torch.float32, device=dev())
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        B.pip_margin(t, p, out=out, stream=s)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    out.zero_()
+    with torch.cuda.graph(g):
+        B.pip_margin(t, p, out=out)
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), eager.view(np.uint32))
+    t.close()
+
+
 # ----------------------------------------------------------------- full size, sampled
 
 def _sample(rng, M, k):
