@@ -246,12 +246,15 @@ def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--gpus", type=int, default=1,
+                    help="GPUs of the job (one rank each under torch.distributed.run; weak scaling)")
+    ap.add_argument("--steps", type=int, default=200, help="timed steps (one pip_test call each)")
+    ap.add_argument("--warmup", type=int, default=20, help="untimed warm-up steps (at least 3)")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"],
+                    help="reference: the CPU oracle timed on bounded samples of the same workload")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing on the host")
+    ap.add_argument("--no-comparators", action="store_true",
+                    help="skip the sign-of-offset, ray-crossing and plain fp64 kernels")
     ap.add_argument("--points", type=int, default=NUM_POINTS,
                     help="points of the workload (default the full 2^26; smaller only for profiling)")
     ap.add_argument("--workload", default=WORKLOAD,
