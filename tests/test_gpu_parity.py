@@ -566,6 +566,25 @@ def test_margin_pipelined_equals_register_streaming(ints):
     t.close()
 
 
+@pytest.mark.parametrize("M", [1, 2, 3, 33, 4095, 4097])
+def test_margin_pipelined_small_and_ragged_sizes(M):
+    """Point counts around one slice and one tile, odd and even, on the
+    pipelined margin kernel: identical to the register-streaming kernel."""
+    w = wl.vehicle_footprint(m=M, seed=66)
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                      max_points=M)
+    flat = torch.from_numpy(np.ascontiguousarray(w.points).reshape(-1)).to(dev())
+    shifted = torch.zeros(2 * M + 2, dtype=flat.dtype, device=dev())
+    shifted[2:] = flat
+    a = B.pip_margin(t, flat).cpu().numpy()
+    b = B.pip_margin(t, shifted[2:]).cpu().numpy()
+    np.testing.assert_array_equal(a.view(np.uint32), b.view(np.uint32))
+    want = oracle.margin(w.vertices, w.points)
+    tol = 16 * 2 ** -24 * (np.abs(w.points.astype(np.float64)).max(axis=1) + 2 * np.abs(w.vertices).max() + 4.0)
+    assert np.all(np.abs(a.astype(np.float64) - want) <= tol)
+    t.close()
+
+
 def test_margin_ragged_and_all_pairs():
     w = wl.gis_batch(seed=20, num_polygons=30, m_range=(10, 3000))
     v = torch.from_numpy(w.vertices).to(dev())
