@@ -158,7 +158,7 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
                                              unsigned int *__restrict__ qcount)
 {
     float xs[PPL], ys[PPL], m[PPL];
-    bool exin[PPL], valid[PPL];
+    bool valid[PPL];
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
         const int r = 32 * q + lane;
@@ -184,7 +184,9 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
                 y = v.y;
             }
         }
-        exin[q] = INT ? int_exact(x, y) : true;
+        // an integer point that float32 does not hold exactly becomes NaN: the
+        // NaN-propagating min then leaves it undecided, for the exact refine
+        if (INT && !int_exact(x, y)) x = __int_as_float(0x7fc00000);
         xs[q] = CENTER ? x - ox : x;
         ys[q] = CENTER ? y - oy : y;
     }
@@ -235,8 +237,8 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
     for (int q = 0; q < PPL; ++q) {
         // B >= beta0 + beta1 max(|x|, |y|); NaN m or infinite B is never "in"
         const float B = fmaf(b1, fabsf(xs[q]) + fabsf(ys[q]), b0);
-        const bool in = (m[q] >= B) && (!INT || exin[q]) && valid[q];
-        unc[q] = (!(fabsf(m[q]) >= B) || (INT && !exin[q])) && valid[q];
+        const bool in = (m[q] >= B) && valid[q];
+        unc[q] = !(fabsf(m[q]) >= B) && valid[q];
         any |= unc[q];
         w_in[q] = __ballot_sync(0xffffffffu, in);
     }
