@@ -258,11 +258,14 @@ pip_status pip_test_voronoi_fp64(const pip_tables *t, const float *d_points,
  * mirrored generators (Eq. 8) and the centroid (Eq. 3-4) to the vertices, and
  * through the rigid transform to the poses.  Each call rebuilds the
  * generators from the vertices (nothing is carried from forward to
- * backward).  Each block keeps float32 partial sums; the backward pass's
- * per-edge sums go to per-thread shared-memory slots for up to 16 edges (a
- * fixed order, so the result is reproducible) and to per-warp slots by
- * shared-memory atomics above (order not fixed).  The per-block partials are
- * fp64 and are added in a fixed order.
+ * backward).  The bulk margins are float32; for every (pose, point) pair
+ * with a nonzero gradient the backward pass re-decides the argmax edge and
+ * re-evaluates its margin in float-float arithmetic (exact point offset,
+ * two-part fp64-derived coefficients), so that dL/dm carries no float32
+ * margin error.  Per-edge sums go to per-thread float32 shared-memory slots
+ * for up to 16 edges (a fixed order, reproducible) and to per-warp slots by
+ * shared-memory atomics above (order not fixed); each block adds them in
+ * fp64, and the per-block partials are added in fp64 in a fixed order.
  *
  *   d_vertices   device float [num_vertices][2], 3..64 vertices, 8-byte aligned
  *   d_poses      device float [num_poses][3] = (t_x, t_y, theta)

@@ -13,16 +13,22 @@
 // between forward and backward) inside a caller-provided workspace.
 //
 // Layout of the work: block (tile, pose) takes one pose and kPenPoints
-// points.  At block start one thread per edge folds the pose into the edge's
-// coefficients (fp64, rounded once), so that a margin term is two FMAs on the
-// world point; for up to 16 edges the coefficients then sit in registers.
-// Every thread keeps float32 partial sums, the block reduces them in fp64
-// into its own slot of the workspace, and a final kernel adds the slots in a
-// fixed order.  In the backward pass only the (pose, point) pairs with a
-// nonzero gradient (the points within ~87 tau of the footprint, where the
-// float32 sigmoid has not underflowed) need the argmax edge and the per-edge
-// sums; each warp queues those pairs in shared memory and resolves them 32
-// at a time, so that a warp does not take that path for a single near point.
+// points.  One thread per edge first folds each pose into the edge's
+// coefficients (fp64 from the fp64 generators, kept as a rounded float32 part
+// and its float32 remainder), so that a margin term is two FMAs on the world
+// point; for up to 16 edges the rounded parts then sit in registers.  The
+// forward pass keeps float32 partial sums per thread and reduces them in fp64
+// per block; a final kernel adds the block slots in a fixed order.  In the
+// backward pass only the (pose, point) pairs with a nonzero gradient (the
+// points within ~87 tau of the footprint, where the float32 sigmoid has not
+// underflowed) need the argmax edge and the per-edge sums; each warp queues
+// those pairs in shared memory and resolves them 32 at a time, one pair per
+// lane.  For each such pair the argmax edge is re-decided and its margin
+// re-evaluated in float-float arithmetic (the point's exact offset from the
+// pose times the two-part coefficients, every edge within the float32 terms'
+// rounding bound of the max taking part), the sigmoid takes a first-order
+// correction for the low part of z, and per-lane float32 slots gather each
+// edge's sums, which the block adds in fp64.
 #include <stdlib.h>
 
 #include "pip_prepare_kernel.cuh"
@@ -46,7 +52,8 @@ struct PenWorkspace {
     double *edge_part;   // [n][3][blocks]  (sum g, sum g x, sum g y) per argmax edge
     double *edge_stage;  // [n][3][kEdgeChunks]  first-level sums of edge_part
     double *pose_sum;    // [3][P]  reduced
-    float4 *pose_coef;  // [P][kPoseStride]  per-pose affine forms (w'_x, w'_y, t', 0)
+    float4 *pose_coef;  // [P][kPoseStride]  per-pose affine forms (w'_x, w'_y, c', 0), rounded
+    float4 *pose_lo;    // [P][kPoseStride]  what the rounding left: exact - rounded, in float32
     double2 *pose_rot;  // [P]  (cos theta, sin theta)
 };
 
@@ -78,6 +85,7 @@ size_t carve(void *base, int n, int P, int64_t blocks, PenWorkspace *w)
     w->edge_stage = (double *)take((size_t)n * 3 * kEdgeChunks * sizeof(double));
     w->pose_sum = (double *)take((size_t)P * 3 * sizeof(double));
     w->pose_coef = (float4 *)take((size_t)P * kPoseStride * sizeof(float4));
+    w->pose_lo = (float4 *)take((size_t)P * kPoseStride * sizeof(float4));
     w->pose_rot = (double2 *)take((size_t)P * sizeof(double2));
     return off;
 }
@@ -129,27 +137,26 @@ __device__ __forceinline__ float log1p_small(float e)
     return u == 1.f ? e : __logf(u) * __fdividef(e, u - 1.f);
 }
 
-// sigmoid(z) = 1 / (1 + e^-z) from e = e^-|z|, evaluated without overflow
-__device__ __forceinline__ float sigmoid_from(float z, float e)
-{
-    return __fdividef(z >= 0.f ? 1.f : e, 1.f + e);
-}
-
 // Per pose, the margin terms as affine forms of d = p - t (the point relative
 // to the pose's position, world axes):
-//   m_k = xb . w_k - c_k  (xb = R^T d body coordinates, w_k unit normal,
-//   c_k the edge line's offset from the body origin)
+//   m_k = xb . w_k - c_k  (xb = R^T d body coordinates, w_k = (p_k - p0) / |p_k - p0|
+//   the unit normal of edge k, c_k = w_k . (p0 + p_k) / 2 the edge line's
+//   offset from the body origin: the bisector of Eq. 2 passes through the
+//   midpoint of p0 and p_k)
 //       = d . w'_k - c_k,   w'_k = R w_k,
-// formed in fp64 (one block per pose, one thread per edge) and rounded once.
-// Keeping t out of the constant keeps it small: a rounded t . w' (tens of
-// metres) would shift every margin of the pose by the same ~1e-6 m, a bias of
-// ~1e-6 / tau in dL/dm.  d itself is exact for the points near the footprint
-// (the ones with a gradient).  Slots past n hold w' = 0, c = +inf
-// (m_k = -inf never attains the max).
+// formed in fp64 from the fp64 generators (one block per pose, one thread per
+// edge), rounded once to float32 for the bulk margin, with the float32
+// remainder exact - rounded kept beside it for the float-float margin of the
+// backward pass.  Keeping t out of the constant keeps it small: a rounded
+// t . w' (tens of metres) would shift every margin of the pose by the same
+// ~1e-6 m.  Slots past n hold w' = 0, c = +inf (m_k = -inf never attains the
+// max).
 __global__ void __launch_bounds__(64) pose_coef_kernel(const PolyInfo *__restrict__ poly,
-                                                       const float4 *__restrict__ coefn,
+                                                       const double2 *__restrict__ g0tab,
+                                                       const double2 *__restrict__ gktab,
                                                        const float *__restrict__ poses, int P,
-                                                       float4 *__restrict__ pose_coef, double2 *__restrict__ pose_rot)
+                                                       float4 *__restrict__ pose_coef, float4 *__restrict__ pose_lo,
+                                                       double2 *__restrict__ pose_rot)
 {
     const int j = blockIdx.x, k = threadIdx.x;
     if (j >= P) return;
@@ -159,15 +166,19 @@ __global__ void __launch_bounds__(64) pose_coef_kernel(const PolyInfo *__restric
     const double cn = cos(th), sn = sin(th);
     if (k == 0) pose_rot[j] = make_double2(cn, sn);
     for (int e = k; e < kPoseStride; e += blockDim.x) {
-        float4 r = make_float4(0.f, 0.f, INFINITY, 0.f);
+        float4 r = make_float4(0.f, 0.f, INFINITY, 0.f), lo = make_float4(0.f, 0.f, 0.f, 0.f);
         if (e < n) {
-            const float4 c = coefn[e];  // (w_x, w_y, t_k) / |w| in local coordinates x = xb - o
-            const double wx = c.x, wy = c.y;
-            const double ck = (double)c.z + (double)pi.ox * wx + (double)pi.oy * wy;
+            const double2 g0 = g0tab[0], g = gktab[e];
+            const double ux = g.x - g0.x, uy = g.y - g0.y;
+            const double D = sqrt(ux * ux + uy * uy);
+            const double wx = ux / D, wy = uy / D;
+            const double ck = 0.5 * (wx * (g0.x + g.x) + wy * (g0.y + g.y));
             const double wpx = cn * wx - sn * wy, wpy = sn * wx + cn * wy;
             r = make_float4((float)wpx, (float)wpy, (float)ck, 0.f);
+            lo = make_float4((float)(wpx - (double)r.x), (float)(wpy - (double)r.y), (float)(ck - (double)r.z), 0.f);
         }
         pose_coef[(size_t)j * kPoseStride + e] = r;
+        pose_lo[(size_t)j * kPoseStride + e] = lo;
     }
 }
 
@@ -205,16 +216,19 @@ __device__ __forceinline__ float margin_of(const float4 *cs, const float (&w)[NE
 }
 
 // Backward accumulators, per edge (sum g, sum g dx, sum g dy) in shared
-// memory.  NE > 0: per lane, no atomics; a lane's slots are 3 NE + 1 words
-// apart (odd), so that lanes on the same edge hit 32 different banks.
-// NE == 0 (up to 64 edges): per warp, shared-memory atomics.
+// memory, float32, summed over the block in fp64.  NE > 0: per lane, no
+// atomics; a lane's slots are 3 NE + 1 words apart (odd), so that lanes on the
+// same edge hit 32 different banks.  NE == 0 (up to 64 edges): per warp, by
+// shared-memory atomics.  A lane's slot takes at most 64 terms per block (its
+// share of the block's points), in practice a few: the slot sums' rounding is
+// of the order of the products' own.
 template <int NE>
 __host__ __device__ constexpr int lane_words() { return NE > 0 ? 3 * NE + 1 : 3 * kMaxEdges; }
 template <int NE>
 __host__ __device__ constexpr int acc_rows() { return NE > 0 ? kPenThreads : kPenThreads / 32; }
 template <int NE>
 __host__ __device__ constexpr size_t acc_floats() { return (size_t)acc_rows<NE>() * lane_words<NE>(); }
-// per-warp ring of queued pairs (dx, dy, dL/dm, m) after the accumulators
+// per-warp ring of queued pairs (p_x, p_y, m, 0) after the accumulators
 constexpr int kPenQueue = 64;
 template <int NE>
 constexpr size_t acc_bytes()
@@ -222,33 +236,81 @@ constexpr size_t acc_bytes()
     return acc_floats<NE>() * sizeof(float) + (size_t)(kPenThreads / 32) * kPenQueue * sizeof(float4);
 }
 
-// One queued pair: the lowest edge whose term equals the max m takes the
-// gradient g (the subgradient of the max); its slot gathers g, g dx, g dy.
-template <int NE>
-__device__ __forceinline__ void pen_scatter(const float4 *cs, const float (&w)[NE > 0 ? NE : 1][3], int n,
-                                            float *my, float4 e)
+// Error-free transformations (Knuth's two-sum, the FMA product error); the
+// _rn intrinsics keep the compiler from fusing the roundings they rely on.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    int kb = 0;
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+
+// Margin of one edge in float-float: d = (px - tx, py - ty) exactly (two
+// two-sums), times the two-part coefficients (hi + lo), minus c; returns
+// mh + ml with |error| about 2^-44 of the largest term.
+__device__ __forceinline__ void margin_ff(float px, float py, float tx, float ty, float4 hi, float4 lo,
+                                         float &mh, float &ml)
+{
+    float dxh, dxl, dyh, dyl;
+    two_sum(px, -tx, dxh, dxl);
+    two_sum(py, -ty, dyh, dyl);
+    float p1, e1, p2, e2, s1, e3, s2, e4;
+    two_prod(dxh, hi.x, p1, e1);
+    two_prod(dyh, hi.y, p2, e2);
+    two_sum(p1, p2, s1, e3);
+    two_sum(s1, -hi.z, s2, e4);
+    float r = (e1 + e2) + (e3 + e4);
+    r += fmaf(dxh, lo.x, dxl * hi.x) + fmaf(dyh, lo.y, dyl * hi.y) - lo.z;
+    two_sum(s2, r, mh, ml);
+}
+
+// The argmax edge of a queued pair, decided as exactly as the float-float
+// margins allow: every edge whose float32 term lies within `tol` of the
+// float32 max m (tol bounds twice the terms' rounding error) is re-evaluated
+// in float-float and the largest wins, the lowest k among ties.  Nearly
+// always one edge qualifies.  Returns the edge and its margin (mh, ml).
+template <int NE>
+__device__ __forceinline__ int argmax_edge_ff(const float4 *cs, const float4 *cl,
+                                              const float (&w)[NE > 0 ? NE : 1][3], int n, float px,
+                                              float py, float tx, float ty, float m, float &mh, float &ml)
+{
+    const float dx = px - tx, dy = py - ty;  // as in the bulk pass
+    // |fp32 term - exact term| <= 8u (|dx| + |dy| + |c_k| + |term|), |c_k| <= |term| + |dx| + |dy|
+    const float tol = 0x1p-19f * (2.f * (fabsf(dx) + fabsf(dy)) + 2.f * fabsf(m)) + 0x1p-120f;
+    const float lo = m - tol;
+    // candidate edges as a bitmask (n <= 64), then one float-float margin each
+    uint64_t cand = 0;
     if (NE > 0) {
 #pragma unroll
-        for (int k = (NE > 0 ? NE : 1) - 1; k >= 0; --k)
-            if (fmaf(e.x, w[k][0], fmaf(e.y, w[k][1], -w[k][2])) == e.w) kb = k;
+        for (int k = 0; k < (NE > 0 ? NE : 1); ++k)
+            if (fmaf(dx, w[k][0], fmaf(dy, w[k][1], -w[k][2])) >= lo) cand |= 1ull << k;
     } else {
-        for (int k = n - 1; k >= 0; --k) {
+        for (int k = 0; k < n; ++k) {
             const float4 c = cs[k];
-            if (fmaf(e.x, c.x, fmaf(e.y, c.y, -c.z)) == e.w) kb = k;
+            if (fmaf(dx, c.x, fmaf(dy, c.y, -c.z)) >= lo) cand |= 1ull << k;
         }
     }
-    float *slot = my + 3 * kb;
-    if (NE > 0) {
-        slot[0] += e.z;
-        slot[1] += e.z * e.x;
-        slot[2] += e.z * e.y;
-    } else {
-        atomicAdd(&slot[0], e.z);
-        atomicAdd(&slot[1], e.z * e.x);
-        atomicAdd(&slot[2], e.z * e.y);
+    int kb = -1;
+    mh = -INFINITY;
+    ml = 0.f;
+    while (cand) {
+        const int k = __ffsll((long long)cand) - 1;  // ascending k: ties keep the lowest
+        cand &= cand - 1;
+        float h, l;
+        margin_ff(px, py, tx, ty, cs[k], cl[k], h, l);
+        if (h > mh || (h == mh && l > ml)) {
+            kb = k;
+            mh = h;
+            ml = l;
+        }
     }
+    return kb;
 }
 
 // The register count is left to the compiler (58 at 12 edges, 4 blocks per
@@ -256,8 +318,8 @@ __device__ __forceinline__ void pen_scatter(const float4 *cs, const float (&w)[N
 template <int NE, bool BACKWARD>
 __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ pose_coef,
-    const double2 *__restrict__ pose_rot, const float *__restrict__ poses, const float *__restrict__ pts,
-    int64_t M, int nv, float tau, double *__restrict__ loss_part, double *__restrict__ pose_part,
+    const float4 *__restrict__ pose_lo, const double2 *__restrict__ pose_rot, const float *__restrict__ poses,
+    const float *__restrict__ pts, int64_t M, int nv, float tau, double *__restrict__ loss_part, double *__restrict__ pose_part,
     double *__restrict__ edge_part)
 {
     constexpr int kWarps = kPenThreads / 32;
@@ -266,6 +328,7 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
     const int n = poly[0].status == PIP_OK ? poly[0].n : 0;
     const int pose = blockIdx.y;
     const float4 *cs = pose_coef + (size_t)pose * kPoseStride;
+    const float4 *cl = pose_lo + (size_t)pose * kPoseStride;
     float w[NE > 0 ? NE : 1][3];
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
@@ -290,19 +353,40 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
     constexpr int kStep = kPenThreads * kPenUnroll;
     const int lane = threadIdx.x & 31;
     // Backward: the pairs with a possibly nonzero gradient, queued per warp
-    // as (dx, dy, m) and finished 32 at a time.  Below z = -87.34 the float32
-    // e^-|z| flushes to 0, so dL/dm is exactly 0 there (kZCold leaves a
-    // margin).  Head and tail count pairs (warp-uniform).  (Queuing the
+    // as (p_x, p_y, m) and finished 32 at a time.  Below z = -87.34 the
+    // float32 e^-|z| flushes to 0, so dL/dm is exactly 0 there (kZCold leaves
+    // a margin).  Head and tail count pairs (warp-uniform).  (Queuing the
     // forward pass's softplus the same way measured slower: the ballot per
     // pair costs more than the special functions it saves.)
     constexpr float kZCold = -88.f;
     float4 *q = (float4 *)(lane_acc + acc_floats<NE>()) + (threadIdx.x >> 5) * kPenQueue;
     int qh = 0, qt = 0;
+    // One queued pair: its argmax edge and margin in float-float, z = -m / tau
+    // with its remainder, dL/dm = -sigmoid(z) / tau with the first-order term
+    // sigmoid' z_lo; the edge's slot gathers g, g dx, g dy.
     auto finish = [&](int slot) {
         const float4 r = q[slot];
-        const float z = -r.z * inv_tau;
-        const float g = -sigmoid_from(z, exp_neg_abs(z)) * inv_tau;  // dL/dm
-        pen_scatter<NE>(cs, w, n, my, make_float4(r.x, r.y, g, r.z));
+        float mh, ml;
+        const int kb = argmax_edge_ff<NE>(cs, cl, w, n, r.x, r.y, ftx, fty, r.z, mh, ml);
+        if (kb < 0) return;  // a non-finite point: no gradient
+        const float zh = __fmul_rn(-mh, inv_tau);
+        const float zl = -(fmaf(zh, tau, mh) + ml) * inv_tau;  // z - zh
+        const float e = expf(-fabsf(zh));
+        const float inv = __frcp_rn(1.f + e);
+        const float sg = zh >= 0.f ? inv : e * inv;  // sigmoid(zh)
+        const float sc = zh >= 0.f ? e * inv : inv;  // 1 - sigmoid(zh)
+        const float g = -fmaf(sg * sc, zl, sg) * inv_tau;  // dL/dm
+        const float dx = r.x - ftx, dy = r.y - fty;
+        float *slot3 = my + 3 * kb;
+        if (NE > 0) {
+            slot3[0] += g;
+            slot3[1] += g * dx;
+            slot3[2] += g * dy;
+        } else {
+            atomicAdd(&slot3[0], g);
+            atomicAdd(&slot3[1], g * dx);
+            atomicAdd(&slot3[2], g * dy);
+        }
     };
 
     // one (pose, point) pair; every thread of the block calls this the same
@@ -319,7 +403,7 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
         const unsigned bal = __ballot_sync(0xffffffffu, hot);
         if (bal) {
             const int at = (qt + __popc(bal & ((1u << lane) - 1u))) & (kPenQueue - 1);
-            if (hot) q[at] = make_float4(dx, dy, m, 0.f);
+            if (hot) q[at] = make_float4(pt.x, pt.y, m, 0.f);
             qt += __popc(bal);
             if (qt - qh >= 32) {  // at most 63 queued: the ring never overflows
                 __syncwarp();
@@ -372,26 +456,27 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
         if (threadIdx.x == 0) loss_part[blk] = s;
     } else {
         __syncthreads();
-        // per (edge, component) v: warp v % 8 adds the 256 lanes' slots, 8 per
-        // lane then a shuffle tree (float32, fixed order)
+        // per (edge, component) v: warp v % 8 adds the slots of the lanes
+        // (or warps), fp64, a fixed order
         __shared__ double es[kMaxEdges][3];
         const int wid = threadIdx.x >> 5;
         for (int v = wid; v < 3 * n; v += kWarps) {
-            float t = 0.f;
-            for (int r = lane; r < acc_rows<NE>(); r += 32) t += lane_acc[(size_t)r * kLW + v];
+            double t = 0.0;
+            for (int r = lane; r < acc_rows<NE>(); r += 32) t += (double)lane_acc[(size_t)r * kLW + v];
             for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) es[v / 3][v % 3] = (double)t;
+            if (lane == 0) es[v / 3][v % 3] = t;
         }
         __syncthreads();
         __shared__ double pg[kMaxEdges][3];
         const int k = threadIdx.x;
         if (k < n) {
             const double S = es[k][0], Dx = es[k][1], Dy = es[k][2];
-            const float4 c = cs[k];
+            const float4 c = cs[k], c2 = cl[k];
+            const double wx = (double)c.x + (double)c2.x, wy = (double)c.y + (double)c2.y;
             // dm/dt = -w',  dm/dtheta = (p - t) x w' = dy w'_x - dx w'_y
-            pg[k][0] = -S * c.x;
-            pg[k][1] = -S * c.y;
-            pg[k][2] = Dy * c.x - Dx * c.y;
+            pg[k][0] = -S * wx;
+            pg[k][1] = -S * wy;
+            pg[k][2] = Dy * wx - Dx * wy;
             // body coordinates: xb = R^T (p - t)
             const double2 rc = pose_rot[pose];
             edge_part[(size_t)(3 * k) * nb + blk] = S;
@@ -545,7 +630,7 @@ void launch_penalty(int n, dim3 grid, cudaStream_t s, const PenWorkspace &w, con
                     const float *pts, int64_t M, float tau)
 {
     const int P = (int)grid.y;
-    pose_coef_kernel<<<P, 64, 0, s>>>(w.poly, w.coefn, poses, P, w.pose_coef, w.pose_rot);
+    pose_coef_kernel<<<P, 64, 0, s>>>(w.poly, w.g0, w.gk, poses, P, w.pose_coef, w.pose_lo, w.pose_rot);
     // the backward pass's accumulators and queues (up to 57 KiB at 16 edges)
     // with the static reduction buffers pass the default 48 KiB limit
 #define PIP_PEN(NE)                                                                                     \
@@ -554,7 +639,8 @@ void launch_penalty(int n, dim3 grid, cudaStream_t s, const PenWorkspace &w, con
             cudaFuncSetAttribute(penalty_kernel<NE, BACKWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  (int)acc_bytes<NE>());                                                 \
         penalty_kernel<NE, BACKWARD><<<grid, kPenThreads, BACKWARD ? acc_bytes<NE>() : 0, s>>>(          \
-            w.poly, w.pose_coef, w.pose_rot, poses, pts, M, n, tau, w.loss_part, w.pose_part, w.edge_part); \
+            w.poly, w.pose_coef, w.pose_lo, w.pose_rot, poses, pts, M, n, tau, w.loss_part, w.pose_part,  \
+            w.edge_part);                                                                                 \
     } while (0)
     if (n <= 4) PIP_PEN(4);
     else if (n <= 8) PIP_PEN(8);
