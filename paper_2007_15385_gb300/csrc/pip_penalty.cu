@@ -36,7 +36,7 @@
 namespace {
 
 constexpr int kPenThreads = 256;
-constexpr int kPenPoints = 16384;  // points per block
+constexpr int kPenPoints = 32768;  // points per block
 
 struct PenWorkspace {
     PolyInfo *poly;
@@ -228,12 +228,14 @@ template <int NE>
 __host__ __device__ constexpr int acc_rows() { return NE > 0 ? kPenThreads : kPenThreads / 32; }
 template <int NE>
 __host__ __device__ constexpr size_t acc_floats() { return (size_t)acc_rows<NE>() * lane_words<NE>(); }
-// per-warp ring of queued pairs (p_x, p_y, m, 0) after the accumulators
-constexpr int kPenQueue = 64;
+// per-warp ring of queued pairs after the accumulators, three float arrays
+// (p_x, p_y, m); drained at most every second pair, so it holds up to
+// 31 + 2 x 32 entries
+constexpr int kPenQueue = 128;
 template <int NE>
 constexpr size_t acc_bytes()
 {
-    return acc_floats<NE>() * sizeof(float) + (size_t)(kPenThreads / 32) * kPenQueue * sizeof(float4);
+    return acc_floats<NE>() * sizeof(float) + (size_t)(kPenThreads / 32) * kPenQueue * 3 * sizeof(float);
 }
 
 // Error-free transformations (Knuth's two-sum, the FMA product error); the
@@ -359,20 +361,21 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
     // forward pass's softplus the same way measured slower: the ballot per
     // pair costs more than the special functions it saves.)
     constexpr float kZCold = -88.f;
-    float4 *q = (float4 *)(lane_acc + acc_floats<NE>()) + (threadIdx.x >> 5) * kPenQueue;
+    float *qx = lane_acc + acc_floats<NE>() + (size_t)(threadIdx.x >> 5) * 3 * kPenQueue;
+    float *qy = qx + kPenQueue, *qm = qy + kPenQueue;
     int qh = 0, qt = 0;
     // One queued pair: its argmax edge and margin in float-float, z = -m / tau
     // with its remainder, dL/dm = -sigmoid(z) / tau with the first-order term
     // sigmoid' z_lo; the edge's slot gathers g, g dx, g dy.
     auto finish = [&](int slot) {
-        const float4 r = q[slot];
+        const float4 r = make_float4(qx[slot], qy[slot], qm[slot], 0.f);
         float mh, ml;
         const int kb = argmax_edge_ff<NE>(cs, cl, w, n, r.x, r.y, ftx, fty, r.z, mh, ml);
         if (kb < 0) return;  // a non-finite point: no gradient
         const float zh = __fmul_rn(-mh, inv_tau);
         const float zl = -(fmaf(zh, tau, mh) + ml) * inv_tau;  // z - zh
         const float e = expf(-fabsf(zh));
-        const float inv = __frcp_rn(1.f + e);
+        const float inv = __fdividef(1.f, 1.f + e);
         const float sg = zh >= 0.f ? inv : e * inv;  // sigmoid(zh)
         const float sc = zh >= 0.f ? e * inv : inv;  // 1 - sigmoid(zh)
         const float g = -fmaf(sg * sc, zl, sg) * inv_tau;  // dL/dm
@@ -403,14 +406,21 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
         const unsigned bal = __ballot_sync(0xffffffffu, hot);
         if (bal) {
             const int at = (qt + __popc(bal & ((1u << lane) - 1u))) & (kPenQueue - 1);
-            if (hot) q[at] = make_float4(pt.x, pt.y, m, 0.f);
-            qt += __popc(bal);
-            if (qt - qh >= 32) {  // at most 63 queued: the ring never overflows
-                __syncwarp();
-                finish((qh + lane) & (kPenQueue - 1));
-                qh += 32;
-                __syncwarp();  // finished slots are refilled next
+            if (hot) {
+                qx[at] = pt.x;
+                qy[at] = pt.y;
+                qm[at] = m;
             }
+            qt += __popc(bal);
+        }
+    };
+    // finishes whole groups of 32 queued pairs (called after every second pair)
+    auto drain = [&]() {
+        while (qt - qh >= 32) {
+            __syncwarp();
+            finish((qh + lane) & (kPenQueue - 1));
+            qh += 32;
+            __syncwarp();  // finished slots are refilled next
         }
     };
     // Steps of kStep points, kPenUnroll per thread, with the next step's
@@ -428,8 +438,10 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
         };
         auto eval = [&](int st, const float2 (&p)[kPenUnroll]) {
 #pragma unroll
-            for (int u = 0; u < kPenUnroll; ++u)
+            for (int u = 0; u < kPenUnroll; ++u) {
                 pair(p[u], FULL || st * kStep + u * kPenThreads + (int)threadIdx.x < cnt);
+                if (BACKWARD && (u & 1)) drain();
+            }
         };
         float2 a[kPenUnroll], b[kPenUnroll];
         load(0, a);
