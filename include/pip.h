@@ -316,7 +316,9 @@ pip_status pip_penalty_backward(const float *d_vertices, int32_t num_vertices, c
  * before any stream capture.  All calls share the one scratch array and it
  * keeps the last call's contents (each call clears its own counters first):
  * calls that overlap on the GPU -- on different streams, or from host threads
- * without ordering -- race on it and must not be issued.
+ * without ordering -- race on it and must not be issued.  The looked-up
+ * address is kept for the life of the process: after cudaDeviceReset on a
+ * device, do not call this entry point on that device again.
  * ------------------------------------------------------------------------ */
 pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype vdtype, int32_t num_vertices,
                                    const void *d_points, pip_dtype pdtype, int64_t num_points,

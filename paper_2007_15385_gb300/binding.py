@@ -409,16 +409,30 @@ def pip_test_single_noalloc(vertices: torch.Tensor, points: torch.Tensor, mask: 
                             status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """One polygon against points with no device allocation inside the call (for callers that
     cannot allocate: fixed-rate control loops, hosts that own the memory pool).  The caller
-    passes every buffer; scratch is a static array inside libpip shared by all calls."""
-    _dev(vertices, "vertices")
-    _dev(points, "points")
-    _dev(mask, "mask")
+    passes every buffer; scratch is a static array inside libpip shared by all calls.  Every
+    tensor must live on the same CUDA device; the call runs with that device current."""
+    named = [(vertices, "vertices"), (points, "points"), (mask, "mask")]
+    if status is not None:
+        named.append((status, "status"))
+    for t_, nm in named:
+        _dev(t_, nm)
+    device = vertices.device
+    for t_, nm in named:
+        if t_.device != device:
+            raise ValueError("%s is on %s, vertices on %s: all tensors must share one device"
+                             % (nm, t_.device, device))
     M = points.numel() // 2
-    _check(lib().pip_test_single_noalloc(vertices.data_ptr(), _dtype_code(vertices),
-                                         vertices.numel() // 2, points.data_ptr() if M else None,
-                                         _dtype_code(points), M, mask.data_ptr() if M else None,
-                                         status.data_ptr() if status is not None else None,
-                                         _stream(stream)), "pip_test_single_noalloc")
+    if mask.dtype != torch.int32 or mask.numel() < (M + 31) // 32:
+        raise ValueError("mask must be int32 with at least ceil(num_points / 32) = %d words"
+                         % ((M + 31) // 32))
+    if status is not None and (status.dtype != torch.int32 or status.numel() < 1):
+        raise ValueError("status must be an int32 tensor of at least one element")
+    with torch.cuda.device(device):
+        _check(lib().pip_test_single_noalloc(vertices.data_ptr(), _dtype_code(vertices),
+                                             vertices.numel() // 2, points.data_ptr() if M else None,
+                                             _dtype_code(points), M, mask.data_ptr() if M else None,
+                                             status.data_ptr() if status is not None else None,
+                                             _stream(stream)), "pip_test_single_noalloc")
     return mask
 
 

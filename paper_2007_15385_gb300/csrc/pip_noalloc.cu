@@ -17,7 +17,9 @@
 // for the life of the process; every call shares it and it keeps the last
 // call's contents, so each call clears its counters first, and calls that
 // overlap on the GPU (different streams, or different host threads without
-// ordering) race on it.
+// ordering) race on it.  The scratch address is looked up once per device and
+// kept; cudaDeviceReset destroys the context that holds the array, so after a
+// reset this entry point must not be called again in the same process.
 #include <mutex>
 
 #include "pip_prepare_kernel.cuh"
@@ -147,7 +149,13 @@ extern "C" pip_status pip_test_single_noalloc(const void *d_vertices, pip_dtype 
     A.mask = d_mask;
     A.first_hit = nullptr;
     A.iedge = s->iedge;
-    refine_kernel<false><<<num_sms * 2, kThreads, 0, cs>>>(A, kSingle);
+    // as pip_test: int64 cross products, one thread a point, when both inputs
+    // are int32; otherwise the per-thread fp64 Voronoi form with the exact
+    // orientation predicate behind it
+    if (vdtype == PIP_I32 && pdtype == PIP_I32)
+        refine_kernel<true><<<num_sms * 8, kThreads, 0, cs>>>(A, kSingle);
+    else
+        refine_kernel<false><<<num_sms * 2, kThreads, 0, cs>>>(A, kSingle);
     PIP_CUDA_TRY(cudaGetLastError());
     return PIP_OK;
 }
