@@ -9,8 +9,13 @@ meets every edge).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank runs the whole workload on its own GPU (weak
-scaling, no data-path collective); rank 0 prints one JSON line.
+At one GPU the line also carries a ``workloads`` object: the octagon, the
+ragged GIS batch, the GIS all-pairs first hit, the integer hulls and the
+collision penalty, each with its call and kernel times, HBM and FP32 rooflines
+(the FP32 peak measured in the same run by a pure-FFMA kernel, beside the
+nominal one), refine fraction, CUDA-graph replay, comparators and the oracle on
+a bounded sample.  Under torchrun each rank runs the headline workload on its
+own GPU (weak scaling, no data-path collective); rank 0 prints one JSON line.
 ``--impl reference`` times the CPU oracle (exact predicate, one thread) on a
 bounded sample of the same workload instead.
 """
@@ -39,9 +44,8 @@ NUM_POINTS = 1 << 26
 FALLBACK_HBM_GBS = 6800.0
 
 # dram bytes (read + write) per launch of the pipelined kernel on this
-# workload, from one ncu capture (profiles/stream_tma_kernel_vehicle_footprint.md)
-# of 2^25 points scaled by 2 to the 2^26-point launch,
-# valid only while the kernel sources hash to the value recorded with it.
+# workload, from one ncu capture of 2^25 points scaled by 2 to the 2^26-point
+# launch, valid only while the kernel sources hash to the value recorded with it.
 NCU_TRAFFIC = {"bytes": 548029440, "sources_sha": "b192a863611cdb65"}
 # GB300 HBM3e nominal bandwidth, reported beside the measured-peak fraction
 NOMINAL_HBM_GBS = 7900.0
@@ -253,6 +257,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"],
                     help="reference: the CPU oracle timed on bounded samples of the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing on the host")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the headline step (no per-workload objects)")
     ap.add_argument("--no-comparators", action="store_true",
                     help="skip the sign-of-offset, ray-crossing and plain fp64 kernels")
     ap.add_argument("--points", type=int, default=NUM_POINTS,
@@ -377,6 +383,7 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / e2e_steps
     e2e_value = whole_job_rate(tests_per_step, world, e2e_ms)
+    h2d_bytes, d2h_bytes = int(p_host.numel() * 4), int(mask_host.numel() * 4)
 
     # same-chip comparators on the same workload (Alg. 2, Alg. 1, plain fp64 Alg. 5)
     comparators = {}
@@ -409,6 +416,24 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_run(w, 1 << 25)
 
+    # every other configuration on the same GPU, apart from the headline step:
+    # one object per workload (N = 1 only; the scaling runs time the headline)
+    workloads, fma_peak, wclk = None, None, None
+    if world == 1 and not args.headline_only:
+        del p_host, mask_host
+        torch.cuda.empty_cache()
+        fma_peak = measure_fma_peak(B, dev, stream)
+        wclocks = ClockSampler(local)
+        wclocks.start()
+        workloads = {}
+        for name in WORKLOADS:
+            workloads[name] = bench_workload(name, B, wl, dev, stream, max(args.steps, 20), args.warmup, fma_peak,
+                                             2070.0, with_cpu=not args.no_cpu_baseline)
+            torch.cuda.empty_cache()
+        wclk = wclocks.stop()
+        for r in workloads.values():
+            renominal(r, wclk.get("sm_mhz"))
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,8 +448,7 @@ def main():
                        "stream_variant": variant},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": int(p_host.numel() * 4),
-                    "d2h_bytes_per_step": int(mask_host.numel() * 4)},
+                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes},
             "gpu_launches": calls_launches * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -437,6 +461,10 @@ def main():
             "margin": margin,
             "cpu_baseline": cpu,
         }
+        if workloads is not None:
+            line["fp32_fma_peak"] = fma_peak
+            line["workloads"] = workloads
+            line["workloads_clocks"] = wclk
         print(json.dumps(line))
     t.close()
     if world > 1:
@@ -445,10 +473,59 @@ def main():
 
 
 def fp32_fma_peak_tflops(sm_mhz: float) -> tuple[float, int]:
-    """#SM x 128 FP32 lanes x 2 flop x clock (clock sampled during the run)."""
+    """Nominal: #SM x 128 FP32 lanes x 2 flop x clock (clock sampled during the run)."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms
+
+
+def measure_fma_peak(B, dev, stream, reps: int = 5) -> dict:
+    """Measured FP32 FMA throughput: pip_fma_peak (8 independent FMA chains per
+    thread, 8 blocks of 256 threads per SM) timed with CUDA events."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(8 * sms * 256, dtype=torch.float32, device=dev)
+    B.pip_fma_peak(sink)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fmas = 0
+    for _ in range(reps):
+        fmas += B.pip_fma_peak(sink)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"tflops": 2.0 * fmas / (ms * 1e-3) / 1e12, "kernel": "fma_peak_kernel (pip_fma_peak)",
+            "ms_per_launch": ms / reps, "fmas_per_launch": fmas // reps}
+
+
+def fma_roofline(flops: float, kernel_ms: float, measured: dict | None, sm_mhz: float) -> dict:
+    """FP32 roofline of a kernel doing `flops` in `kernel_ms`, against the peak
+    measured in this run and against the nominal one at the sampled clock."""
+    nominal, sms = fp32_fma_peak_tflops(sm_mhz or 2070.0)
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    out = {"bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
+           "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,
+           "nominal_kind": "%d SMs x 128 FP32 FMA lanes x 2 flop x sampled SM clock" % sms}
+    if measured:
+        out.update({"peak": measured["tflops"], "frac": achieved / measured["tflops"],
+                    "peak_kind": "measured in this run: pip_fma_peak, a pure FFMA kernel"})
+    else:
+        out.update({"peak": nominal, "frac": achieved / nominal, "peak_kind": "nominal"})
+    return out
+
+
+def renominal(d: dict, sm_mhz: float) -> None:
+    """Re-states every FP32 roofline in `d` against the nominal peak at the SM
+    clock sampled over the run (known only once the sampler stops)."""
+    if not sm_mhz:
+        return
+    for k, r in d.items():
+        if k.startswith("fma_roofline") and isinstance(r, dict):
+            nominal, _ = fp32_fma_peak_tflops(sm_mhz)
+            r["nominal_peak"] = nominal
+            r["frac_of_nominal"] = r["achieved"] / nominal
 
 
 def time_steps(fn, steps: int, warmup: int, stream) -> float:
@@ -565,70 +642,109 @@ def run_raster(args):
     return 0
 
 
-def run_other(args):
-    """One JSON line for a workload other than the headline (same metric and unit)."""
+def workload_cpu_baseline(name: str, w) -> dict:
+    """The oracle on a bounded sample of one workload (about a second or two on
+    one host thread), as Gtests/s in the full-work convention."""
+    import oracle
+    n = w.edges()
+    if name in ("gis_batch", "integer_hulls"):
+        K = 16 if name == "gis_batch" else 512
+        vo, po = w.vertex_offsets, w.point_offsets
+        v = w.vertices[:vo[K]]
+        q = w.points[:po[K]]
+        tests = int((np.diff(po[:K + 1]) * n[:K]).sum())
+        t0 = time.perf_counter()
+        oracle.inside_exact_ragged(v, vo[:K + 1], q, po[:K + 1])
+        dt = time.perf_counter() - t0
+        sample = "the first %d polygons with their %d points, oracle.inside_exact_ragged, one thread, %.2f s" % (
+            K, len(q), dt)
+    elif name == "gis_all_pairs":
+        m = 4096
+        tests = m * int(n.sum())
+        t0 = time.perf_counter()
+        oracle.first_hit_exact(w.vertices, w.vertex_offsets, w.points[:m])
+        dt = time.perf_counter() - t0
+        sample = "the first %d points against all %d polygons, oracle.first_hit_exact (early exit), one thread, " \
+                 "%.2f s" % (m, w.num_polygons, dt)
+    elif name == "footprint_trajectory":
+        k = 4
+        poses = w.extra["poses"][:k]
+        tests = k * w.num_points * int(n[0])
+        t0 = time.perf_counter()
+        oracle.penalty(w.vertices.astype(np.float64), poses.astype(np.float64), w.points.astype(np.float64),
+                       float(np.float32(w.extra["tau"])))
+        dt = time.perf_counter() - t0
+        sample = "the first %d poses x all %d points, oracle.penalty (loss and every gradient, fp64), one " \
+                 "thread, %.2f s" % (k, w.num_points, dt)
+    else:
+        tests = w.num_points * int(n.sum())
+        t0 = time.perf_counter()
+        oracle.inside_exact(w.vertices, w.points)
+        dt = time.perf_counter() - t0
+        sample = "all %d points, oracle.inside_exact, one thread, %.2f s" % (w.num_points, dt)
+    return {"value": tests / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+
+WORKLOADS = ("unit_circle_octagon", "gis_batch", "gis_all_pairs", "integer_hulls", "footprint_trajectory")
+
+
+def bench_workload(name: str, B, wl, dev, stream, steps: int, warmup: int, fma_peak: dict | None,
+                   sm_mhz: float, polygons: int = 0, with_cpu: bool = True) -> dict:
+    """Every measurement of one workload other than the headline: the call's
+    time, the kernels' times, the rooflines, the refine fraction, the call
+    replayed as a CUDA graph, the comparators where they apply and the oracle
+    on a bounded sample.  Inputs are resident in HBM before timing starts."""
     import torch
-
-    from paper_2007_15385_gb300 import binding as B
-    from paper_2007_15385_gb300 import workloads as wl
-
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
-    gen = {"gis_batch": wl.gis_batch, "gis_all_pairs": wl.gis_all_pairs,
-           "integer_hulls": wl.integer_hulls, "footprint_trajectory": wl.footprint_trajectory,
-           "unit_circle_octagon": wl.unit_circle_octagon}[args.workload]
-    w = gen(num_polygons=args.polygons) if args.polygons > 0 and args.workload in (
-        "gis_batch", "gis_all_pairs", "integer_hulls") else gen()
+    gen = getattr(wl, name)
+    w = gen(num_polygons=polygons) if polygons > 0 and name in ("gis_batch", "gis_all_pairs",
+                                                                   "integer_hulls") else gen()
     v = torch.from_numpy(w.vertices).to(dev)
     vo = torch.from_numpy(w.vertex_offsets).to(dev)
     p = torch.from_numpy(w.points).to(dev)
     po = torch.from_numpy(w.point_offsets).to(dev) if w.point_offsets is not None else None
     M = w.num_points
     tests = w.tests()
-    clocks = ClockSampler(dev.index or 0)
-    clocks.start()
-    extra = {}
-    if args.workload == "footprint_trajectory":
+    out = {"config": {"num_points": M, "num_polygons": w.num_polygons, "tests_per_step": tests}}
+    if name == "footprint_trajectory":
         poses = torch.from_numpy(w.extra["poses"]).to(dev)
         tau = w.extra["tau"]
         ws = torch.empty(B.pip_penalty_workspace_bytes(len(w.vertices), len(poses), M),
                          dtype=torch.uint8, device=dev)
         n = len(w.vertices)
         tests = len(poses) * M * n
-        fwd = time_steps(lambda: B.pip_penalty_forward(v, poses, p, tau, workspace=ws),
-                         args.steps, args.warmup, stream)
-        bwd = time_steps(lambda: B.pip_penalty_backward(v, poses, p, tau, workspace=ws),
-                         args.steps, args.warmup, stream)
-        ms = fwd
-        extra = {"forward_ms": fwd, "backward_ms": bwd,
-                 "forward_Gtests_per_s": tests / (fwd * 1e-3) / 1e9,
-                 "backward_Gtests_per_s": tests / (bwd * 1e-3) / 1e9,
-                 "pairs": len(poses) * M}
-        launches = 5  # begin, prepare, pose coefficients, penalty, loss reduction
+        fwd = time_steps(lambda: B.pip_penalty_forward(v, poses, p, tau, workspace=ws), steps, warmup, stream)
+        bwd = time_steps(lambda: B.pip_penalty_backward(v, poses, p, tau, workspace=ws), steps, warmup, stream)
+        out["config"].update({"num_poses": len(poses), "tau": tau, "tests_per_step": tests,
+                              "pairs": len(poses) * M})
+        out.update({"ms_per_step": fwd, "Gtests_per_s": tests / (fwd * 1e-3) / 1e9,
+                    "forward_ms": fwd, "backward_ms": bwd,
+                    "forward_Gtests_per_s": tests / (fwd * 1e-3) / 1e9,
+                    "backward_Gtests_per_s": tests / (bwd * 1e-3) / 1e9,
+                    "gpu_launches_per_step": {"forward": 6, "backward": 7},
+                    # every edge term is two FMAs (4 flops)
+                    "fma_roofline": fma_roofline(4.0 * tests, fwd, fma_peak, sm_mhz),
+                    "fma_roofline_backward": fma_roofline(4.0 * tests, bwd, fma_peak, sm_mhz)})
     else:
         t = B.pip_prepare(v, vo, max_points=M)
-        mode = B.PIP_MASK | (B.PIP_FIRST_HIT if args.workload == "gis_all_pairs" else 0)
+        mode = B.PIP_MASK | (B.PIP_FIRST_HIT if name == "gis_all_pairs" else 0)
         mask = torch.empty((M + 31) // 32, dtype=torch.int32, device=dev)
         hit = torch.empty(M, dtype=torch.int32, device=dev) if mode & B.PIP_FIRST_HIT else None
         call = lambda: B.pip_test(t, p, po, mode=mode, mask=mask, first_hit=hit)
-        extra = {}
         if po is not None and p.data_ptr() % 16 == 0:
             # tile shape of the pipelined batch kernel, tuned on this batch (not timed)
-            extra["batch_variant"], _ = B.pip_autotune_batch(t, p, po, mask, reps=3)
-        for _ in range(args.warmup):
-            call()
-        torch.cuda.synchronize()
-        ms = time_steps(call, args.steps, 0, stream)
+            out["batch_variant"], _ = B.pip_autotune_batch(t, p, po, mask, reps=3)
+        ms = time_steps(call, steps, warmup, stream)
         # per-call kernel events in a separate pass, out of the step time
         B.pip_timing(t, True)
-        for _ in range(args.steps):
+        for _ in range(steps):
             call()
         calls, bulk_ms, refine_ms = B.pip_timing_read(t)
         B.pip_timing(t, False)
         _, refined = B.pip_get_status(t)
-        extra.update({"bulk_kernel_ms": bulk_ms / max(1, calls), "refine_kernel_ms": refine_ms / max(1, calls),
-                      "refined_points_per_step": refined, "refine_fraction": refined / max(1, M)})
+        bulk = bulk_ms / max(1, calls)
+        out.update({"ms_per_step": ms, "Gtests_per_s": tests / (ms * 1e-3) / 1e9,
+                    "bulk_kernel_ms": bulk, "refine_kernel_ms": refine_ms / max(1, calls),
+                    "refined_points_per_step": refined, "refine_fraction": refined / max(1, M)})
         # the whole call (setup, bulk, refine) captured once as a CUDA graph, replayed per step
         gs = torch.cuda.Stream()
         gs.wait_stream(stream)
@@ -639,47 +755,83 @@ def run_other(args):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
             call()
-        extra["graph_ms_per_step"] = time_steps(graph.replay, args.steps, 3, stream)
-        if args.workload == "gis_all_pairs":
+        out["graph_ms_per_step"] = time_steps(graph.replay, steps, 3, stream)
+        del graph
+        if name == "gis_all_pairs":
             # bounding-box cull and early stop (PIP_CULL): same results, less work;
             # reported apart as an effective rate, not as the full-work value
             cull = lambda: B.pip_test(t, p, po, mode=mode | B.PIP_CULL, mask=mask, first_hit=hit)
-            cms = time_steps(cull, args.steps, 3, stream)
-            extra["culled"] = {"ms_per_step": cms, "effective_Gtests_per_s": tests / (cms * 1e-3) / 1e9,
-                               "note": "PIP_CULL: polygons skipped per warp by bounding box, early stop"}
+            cms = time_steps(cull, steps, 3, stream)
+            out["culled"] = {"ms_per_step": cms, "effective_Gtests_per_s": tests / (cms * 1e-3) / 1e9,
+                             "note": "PIP_CULL: polygons skipped per warp by bounding box, early stop"}
         # our kernels per call: batch = items prefix, item fill, bulk, refine;
         # all pairs = bulk, finalize, refine; one polygon = the pipelined
         # kernel (refine inline), or bulk + refine for unaligned points
         if po is not None:
-            launches = 4
-        elif len(w.vertex_offsets) > 2:
-            launches = 3
+            out["gpu_launches_per_step"] = 4
+        elif w.num_polygons > 1:
+            out["gpu_launches_per_step"] = 3
         else:
-            launches = 1 if p.data_ptr() % 16 == 0 else 2
+            out["gpu_launches_per_step"] = 1 if p.data_ptr() % 16 == 0 else 2
+        if name in ("gis_all_pairs", "gis_batch", "integer_hulls"):
+            # every test is two FMAs (4 flops): s_k = t_k - x w_kx - y w_ky
+            out["fma_roofline"] = fma_roofline(4.0 * tests, bulk, fma_peak, sm_mhz)
+        if name in ("gis_batch", "integer_hulls", "unit_circle_octagon"):
+            peak, kind = measured_peaks()
+            nbytes = M * 8 + ((M + 31) // 32) * 4
+            out["roofline"] = {"bound": "hbm", "achieved": nbytes / (bulk * 1e-3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": nbytes / (bulk * 1e-3) / 1e9 / peak,
+                               "peak_kind": kind + " hbm_gbs", "bytes_per_launch": nbytes,
+                               "kernel_ms": bulk, "call_frac": nbytes / (ms * 1e-3) / 1e9 / peak}
+        if name in ("gis_batch", "integer_hulls", "unit_circle_octagon"):
+            # the paper's comparators on the same points and polygons (float32
+            # listings; integer hulls as float32, exact below 2^24)
+            tc, pc = t, p
+            if w.vertices.dtype != np.float32:
+                tc = B.pip_prepare(v.float(), vo, max_points=M)
+                pc = p.float()
+            comps = {}
+            for cname, fn in (("sign_of_offset_f32", B.pip_test_sign_of_offset),
+                              ("ray_crossing_f32", B.pip_test_ray_crossing),
+                              ("voronoi_plain_fp64", B.pip_test_voronoi_fp64)):
+                cmask = torch.empty_like(mask)
+                cms = time_steps(lambda: fn(tc, pc, po, mask=cmask), 5 if "fp64" in cname else steps, 2, stream)
+                comps[cname] = {"ms": cms, "Gtests_per_s": tests / (cms * 1e-3) / 1e9}
+            out["comparators"] = comps
+            if tc is not t:
+                tc.close()
         t.close()
+    if with_cpu:
+        out["cpu_baseline"] = workload_cpu_baseline(name, w)
+    return out
+
+
+def run_other(args):
+    """One JSON line for a workload other than the headline (same metric and unit)."""
+    import torch
+
+    from paper_2007_15385_gb300 import binding as B
+    from paper_2007_15385_gb300 import workloads as wl
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    fma_peak = measure_fma_peak(B, dev, stream)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    r = bench_workload(args.workload, B, wl, dev, stream, args.steps, args.warmup, fma_peak, 2070.0,
+                       polygons=args.polygons, with_cpu=not args.no_cpu_baseline)
     clk = clocks.stop()
-    value = tests / (ms * 1e-3) / 1e9
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "num_points": M, "num_polygons": w.num_polygons,
-                       "tests_per_step": tests},
-            "clocks": clk, "gpu_launches": launches * args.steps}
-    line.update(extra)
-    if args.workload in ("gis_all_pairs", "footprint_trajectory", "gis_batch", "integer_hulls"):
-        # every test is two FMAs (4 flops): s_k = t_k - x w_kx - y w_ky
-        tflops, sms = fp32_fma_peak_tflops(clk["sm_mhz"] or 2070.0)
-        kernel_ms = extra.get("bulk_kernel_ms", ms)
-        achieved = 4.0 * tests / (kernel_ms * 1e-3) / 1e12
-        line["fma_roofline"] = {"bound": "alu", "achieved": achieved, "peak": tflops, "unit": "TFLOP/s",
-                                "frac": achieved / tflops,
-                                "peak_kind": "%d SMs x 128 FP32 FMA lanes x 2 flop x sampled SM clock" % sms}
-    if args.workload in ("gis_batch", "integer_hulls"):
-        peak, kind = measured_peaks()
-        kernel_ms = extra["bulk_kernel_ms"]
-        achieved = (M * 8 + ((M + 31) // 32) * 4) / (kernel_ms * 1e-3) / 1e9
-        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "peak_kind": kind + " hbm_gbs"}
+    renominal(r, clk.get("sm_mhz"))
+    launches = r.pop("gpu_launches_per_step")
+    if isinstance(launches, dict):
+        launches = sum(launches.values())
+    line = {"metric": METRIC, "value": r.pop("Gtests_per_s"), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict({"workload": args.workload}, **r.pop("config")),
+            "clocks": clk, "gpu_launches": launches * args.steps, "fp32_fma_peak": fma_peak}
+    line.update(r)
     print(json.dumps(line))
     return 0
 

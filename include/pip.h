@@ -357,6 +357,23 @@ pip_status pip_rasterize(const pip_tables *t, int32_t width, int32_t height, flo
                          size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
+ * pip_fma_peak -- the paper has no counterpart to this call; it measures the
+ * float32 FMA throughput of the current GPU, the denominator of the FP32
+ * roofline that the dense all-pairs test and the penalty are reported
+ * against.  Launches blocks_per_sm x #SM blocks of 256 threads, each thread
+ * running 8 independent FMA chains for `iters` x 16 steps; the caller times
+ * the launch (CUDA events on `stream`) and divides *fmas by the time.
+ *
+ *   d_sink       device float [sink_floats], sink_floats >= blocks x 256; the
+ *                kernel never actually writes it (a guarded store that keeps
+ *                the work from being optimised away)
+ *   fmas         receives the number of FMAs the launch performs
+ * Returns PIP_OK, PIP_E_INVALID_ARG or PIP_E_CUDA.
+ * ------------------------------------------------------------------------ */
+pip_status pip_fma_peak(int32_t blocks_per_sm, int32_t iters, float *d_sink, int64_t sink_floats, void *stream,
+                        int64_t *fmas);
+
+/* ------------------------------------------------------------------------
  * pip_selftest_wait_timeout -- the paper has no counterpart to this call; it
  * exercises the failure path that every pipelined kernel takes when one of
  * its waits never completes (a lost producer or consumer).

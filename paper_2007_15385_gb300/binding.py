@@ -55,6 +55,7 @@ SIGNATURES = {
     "pip_test_single_noalloc": (_INT, [_P, _INT, _I32, _P, _INT, _I64, _P, _P, _P]),
     "pip_stream_variant_count": (_I32, []),
     "pip_selftest_wait_timeout": (_INT, [_P, _P, _I64, _P]),
+    "pip_fma_peak": (_INT, [_I32, _I32, _P, _I64, _P, ctypes.POINTER(_I64)]),
     "pip_raster_workspace_bytes": (ctypes.c_size_t, [_I32, _I32, _I32]),
     "pip_rasterize": (_INT, [_P, _I32, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              _P, _P, _P, ctypes.c_size_t, _P]),
@@ -403,6 +404,16 @@ def pip_selftest_wait_timeout(tables: Tables, limit_cycles: int, stream=None) ->
     _check(lib().pip_selftest_wait_timeout(tables, scratch.data_ptr(), int(limit_cycles), _stream(stream)),
            "pip_selftest_wait_timeout")
     tables._keep = scratch  # the copy reads it until the kernel ends
+
+
+def pip_fma_peak(sink: torch.Tensor, blocks_per_sm: int = 8, iters: int = 4096, stream=None) -> int:
+    """Queue the pure float32 FMA kernel on the current device; returns the FMAs it performs
+    (the caller times it).  ``sink`` is a float32 CUDA tensor of at least blocks x 256 elements."""
+    _dev(sink, "sink")
+    fmas = ctypes.c_int64(0)
+    _check(lib().pip_fma_peak(int(blocks_per_sm), int(iters), sink.data_ptr(), sink.numel(), _stream(stream),
+                              ctypes.byref(fmas)), "pip_fma_peak")
+    return int(fmas.value)
 
 
 def pip_test_single_noalloc(vertices: torch.Tensor, points: torch.Tensor, mask: torch.Tensor,
