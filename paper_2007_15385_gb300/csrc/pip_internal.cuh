@@ -91,6 +91,10 @@ struct pip_tables {
     float4 *d_coefn;
     float4 *d_coefp;             // [P][kPadStride] coefficients padded per polygon (all pairs, batch)
     int4 *d_iedge;               // [V] integer polygons: (v_{k-1}, oriented edge k); null for float ones
+    int4 *d_ipad;                // [P][kPadStride] integer polygons: exact edge rows (e_x, -e_y, -C lo, -C hi),
+                                 // zero past n; null for float ones
+    float4 *d_fpad;              // [P][kPadStride] integer polygons: (a_x, a_y, e_x, e_y) in float32, a = v_{k-1},
+                                 // e the oriented edge, zero past n; null for float ones
     pip::PolyInfo *d_poly;
     uint32_t *d_queue;
     uint32_t *d_keys;            // [max_points] all-pairs candidate keys

@@ -105,6 +105,8 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     const size_t o_coefn = take(V * sizeof(float4));
     const size_t o_coefp = take(P * kPadStride * sizeof(float4));
     const size_t o_iedge = take(vdtype == PIP_I32 ? V * sizeof(int4) : 0);
+    const size_t o_ipad = take(vdtype == PIP_I32 ? P * kPadStride * sizeof(int4) : 0);
+    const size_t o_fpad = take(vdtype == PIP_I32 ? P * kPadStride * sizeof(float4) : 0);
     const size_t o_poly = take(P * sizeof(PolyInfo));
     const size_t o_items = take((P + 1) * sizeof(int64_t));
     // items of the pipelined own-polygon kernel: a range [a, b) touches at most
@@ -132,6 +134,8 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     t->d_coefn = (float4 *)(b + o_coefn);
     t->d_coefp = (float4 *)(b + o_coefp);
     t->d_iedge = vdtype == PIP_I32 ? (int4 *)(b + o_iedge) : nullptr;
+    t->d_ipad = vdtype == PIP_I32 ? (int4 *)(b + o_ipad) : nullptr;
+    t->d_fpad = vdtype == PIP_I32 ? (float4 *)(b + o_fpad) : nullptr;
     t->d_poly = (PolyInfo *)(b + o_poly);
     t->d_items = (int64_t *)(b + o_items);
     t->d_ritems = (void *)(b + o_ritems);
@@ -165,9 +169,12 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
         const int threads = 256;
         const int blocks = (int)((P * 32 + threads - 1) / threads);
         pad_coef_kernel<<<blocks, threads, 0, s>>>(t->d_poly, t->d_coef, num_polygons, t->d_coefp);
-        if (t->d_iedge)
+        if (t->d_iedge) {
             int_edge_kernel<<<blocks, threads, 0, s>>>(t->d_poly, (const int2 *)t->d_verts, num_polygons,
                                                        t->d_iedge);
+            int_pad_kernel<<<blocks, threads, 0, s>>>(t->d_poly, (const int2 *)t->d_verts, num_polygons,
+                                                      t->d_ipad, t->d_fpad);
+        }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && num_polygons == 1) {

@@ -281,4 +281,38 @@ __global__ void int_edge_kernel(const PolyInfo *__restrict__ poly, const int2 *_
     }
 }
 
+// Integer polygons, for the exact batch test: per polygon a fixed-stride row
+// of kPadStride edges, edge k as (e_x, -e_y, -C) with e = orient (v_k - v_{k-1})
+// and C = e_x y_{k-1} - e_y x_{k-1}, so that
+//     cross_k(p) = e_x (p_y - y_{k-1}) - e_y (p_x - x_{k-1}) = e_x p_y - e_y p_x - C
+// is two 32 x 32 -> 64-bit multiply-adds, and p is inside (closed) iff every
+// cross_k(p) >= 0.  |v| <= 2^24 and |p| < 2^31 keep every term below 2^57.
+// Rows past n are zero (cross = 0: neutral); invalid polygons are skipped by
+// their status.  The same edges also go to `fpad` as float32 (a_x, a_y, e_x, e_y),
+// a = v_{k-1}, exact for polygons within +-2^22 (the float32 form of the exact
+// test in the batch kernel).
+__global__ void int_pad_kernel(const PolyInfo *__restrict__ poly, const int2 *__restrict__ verts, int P,
+                               int4 *__restrict__ ipad, float4 *__restrict__ fpad)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    if (j >= P) return;
+    const PolyInfo pi = poly[j];
+    const int n = pi.status == PIP_OK ? pi.n : 0;
+    for (int k = lane; k < kPadStride; k += 32) {
+        int4 r = make_int4(0, 0, 0, 0);
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < n) {
+            const int km = k == 0 ? n - 1 : k - 1;
+            const int2 a = verts[pi.voff + km], b = verts[pi.voff + k];
+            const int ex = pi.orient * (b.x - a.x), ey = pi.orient * (b.y - a.y);
+            const long long negC = (long long)ey * a.x - (long long)ex * a.y;
+            r = make_int4(ex, -ey, (int)(unsigned)(negC & 0xffffffffll), (int)(negC >> 32));
+            f = make_float4((float)a.x, (float)a.y, (float)ex, (float)ey);
+        }
+        ipad[(size_t)j * kPadStride + k] = r;
+        fpad[(size_t)j * kPadStride + k] = f;
+    }
+}
+
 }  // namespace

@@ -145,6 +145,41 @@ __global__ void __launch_bounds__(256) ragged_fill_kernel(const int64_t *__restr
     }
 }
 
+// The slice's PPL mask words: words wholly inside the polygon's range are
+// stored (16-byte stores when aligned), words shared with a neighbour are
+// OR-ed into the word the fill kernel zeroed.
+template <int PPL, bool TAIL>
+__device__ __forceinline__ void ragged_store_words(const uint32_t (&w_in)[PPL], int64_t gs, int64_t a, int64_t b,
+                                                   int lane, uint32_t *__restrict__ mask, bool vec_store)
+{
+    uint32_t *mw = mask + (gs >> 5);
+    if (!TAIL) {
+        if (vec_store && (PPL % 4) == 0) {
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < PPL; q += 4)
+                    *(uint4 *)(mw + q) = make_uint4(w_in[q], w_in[q + 1], w_in[q + 2], w_in[q + 3]);
+            }
+        } else {
+            uint32_t myword = 0;
+#pragma unroll
+            for (int q = 0; q < PPL; ++q)
+                if (lane == q) myword = w_in[q];
+            if (lane < PPL) mw[lane] = myword;
+        }
+    } else {
+        uint32_t myword = 0;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            if (lane == q) myword = w_in[q];
+        if (lane < PPL) {
+            const int64_t w0 = gs + 32 * lane;  // first point of this lane's word
+            if (w0 >= a && w0 + 32 <= b) mw[lane] = myword;        // wholly this polygon's
+            else if (w0 < b && w0 + 32 > a && myword) atomicOr(&mw[lane], myword);  // shared, zeroed
+        }
+    }
+}
+
 // One consumer warp, one slice: points gs + [0, 32*PPL) of which [a, b) are
 // polygon j's (TAIL: the slice is not wholly inside; the odd last point of
 // the range is not in the bulk copy and is read from global memory).  An
@@ -265,32 +300,98 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
             base += (unsigned int)__popc(u[q]);
         }
     }
-    uint32_t *mw = mask + (gs >> 5);
-    if (!TAIL) {
-        if (vec_store && (PPL % 4) == 0) {
-            if (lane == 0) {
+    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, lane, mask, vec_store);
+}
+
+// Integer polygon and integer points, decided exactly here: no filter, no
+// queue, no refine.  Edge k of the staged row is (a_x, a_y, e_x, e_y) in
+// float32, a = v_{k-1}, e = orient (v_k - v_{k-1}); p is inside (closed) iff
+// cross_k(p) = e_x d_y - e_y d_x >= 0 for every k, d = p - a.  With every
+// vertex and the warp's points within +-2^22, a, e and d are exact in float32
+// and the sign of the integer cross_k is exact from
+//     w = fl(e_y d_x),  r = e_y d_x - w (one FMA, exact),
+//     f = fl(e_x d_y - w) (one FMA),  cross_k ~ fl(f - r):
+// if |e_x d_y - w| < 2^24, f is exact and f - r = cross_k; otherwise |f| and
+// |e_x d_y - w| exceed |r| (<= 2^22, as |w| <= 2^46) by more than f's
+// rounding, so f - r has the sign of cross_k.  The min over edges of those
+// values is >= 0 iff the point is inside; rows past n are zero (neutral).
+// A warp holding a point beyond +-2^22, or a polygon beyond it, takes the
+// int64 form instead, cross_k = e_x p_y - e_y p_x - C from the polygon's
+// integer row in global memory (two 32 x 32 -> 64-bit multiply-adds).
+template <int PPL, bool TAIL>
+__device__ __forceinline__ void ragged_slice_exact(const float4 *fs, const int4 *__restrict__ irow, int n,
+                                                   bool poly_small, const unsigned char *rows,
+                                                   const void *__restrict__ pts, int64_t gs, int64_t a, int64_t b,
+                                                   int lane, uint32_t *__restrict__ mask, bool vec_store)
+{
+    constexpr int kLim = 1 << 22;
+    int px[PPL], py[PPL];
+    bool valid[PPL];
+    bool small = true;
 #pragma unroll
-                for (int q = 0; q < PPL; q += 4)
-                    *(uint4 *)(mw + q) = make_uint4(w_in[q], w_in[q + 1], w_in[q + 2], w_in[q + 3]);
+    for (int q = 0; q < PPL; ++q) {
+        const int r = 32 * q + lane;
+        const int64_t p = gs + r;
+        int x = 0, y = 0;
+        valid[q] = !TAIL || (p >= a && p < b);
+        if (valid[q]) {
+            if (TAIL && p == b - 1 && (b & 1)) {
+                x = ((const int32_t *)pts)[2 * p];
+                y = ((const int32_t *)pts)[2 * p + 1];
+            } else {
+                const int2 v = ((const int2 *)rows)[r];
+                x = v.x;
+                y = v.y;
             }
-        } else {
-            uint32_t myword = 0;
-#pragma unroll
-            for (int q = 0; q < PPL; ++q)
-                if (lane == q) myword = w_in[q];
-            if (lane < PPL) mw[lane] = myword;
         }
-    } else {
-        uint32_t myword = 0;
-#pragma unroll
-        for (int q = 0; q < PPL; ++q)
-            if (lane == q) myword = w_in[q];
-        if (lane < PPL) {
-            const int64_t w0 = gs + 32 * lane;  // first point of this lane's word
-            if (w0 >= a && w0 + 32 <= b) mw[lane] = myword;        // wholly this polygon's
-            else if (w0 < b && w0 + 32 > a && myword) atomicOr(&mw[lane], myword);  // shared, zeroed
-        }
+        px[q] = x;
+        py[q] = y;
+        small &= x >= -kLim && x <= kLim && y >= -kLim && y <= kLim;
     }
+    const int npad = (n + 3) & ~3;
+    uint32_t w_in[PPL];
+    if (__all_sync(0xffffffffu, small && poly_small)) {
+        float xs[PPL], ys[PPL], m[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            xs[q] = (float)px[q];
+            ys[q] = (float)py[q];
+            m[q] = 0.f;
+        }
+        for (int k = 0; k < npad; k += 2) {
+            const float4 c0 = fs[k], c1 = fs[k + 1];
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                const float dx0 = __fsub_rn(xs[q], c0.x), dy0 = __fsub_rn(ys[q], c0.y);
+                const float w0 = __fmul_rn(c0.w, dx0);
+                const float r0 = fmaf(c0.w, dx0, -w0);
+                const float f0 = fmaf(c0.z, dy0, -w0);
+                const float dx1 = __fsub_rn(xs[q], c1.x), dy1 = __fsub_rn(ys[q], c1.y);
+                const float w1 = __fmul_rn(c1.w, dx1);
+                const float r1 = fmaf(c1.w, dx1, -w1);
+                const float f1 = fmaf(c1.z, dy1, -w1);
+                m[q] = fmin3(m[q], __fsub_rn(f0, r0), __fsub_rn(f1, r1));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) w_in[q] = __ballot_sync(0xffffffffu, valid[q] && m[q] >= 0.f);
+    } else {
+        int neg[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) neg[q] = 0;
+        for (int k = 0; k < npad; ++k) {
+            const int4 e = irow[k];
+            const long long c = (long long)(((unsigned long long)(unsigned)e.w << 32) | (unsigned)e.z);
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                const long long v = (long long)e.y * px[q] + ((long long)e.x * py[q] + c);
+                neg[q] |= (int)(v >> 32);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) w_in[q] = __ballot_sync(0xffffffffu, valid[q] && neg[q] >= 0);
+    }
+    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, lane, mask, vec_store);
 }
 
 // A polygon that failed validation contains no point: its words are zero.
@@ -304,9 +405,14 @@ __device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_
     }
 }
 
-template <int PPL, int STAGES, bool INT>
+// EXACT (integer polygons and points): `coefp` is the table of the polygons'
+// float32 edge rows (a_x, a_y, e_x, e_y) and every point is decided exactly in
+// the consumers (nothing is queued); `ipad` holds the int64 rows for points or
+// polygons beyond +-2^22.
+template <int PPL, int STAGES, bool INT, bool EXACT>
 __global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBlocks) ragged_tma_kernel(
-    const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, const void *__restrict__ pts,
+    const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, const int4 *__restrict__ ipad,
+    const void *__restrict__ pts,
     const RaggedItem *__restrict__ items, const int64_t *__restrict__ prefix, int P,
     unsigned int *__restrict__ counters, uint32_t *__restrict__ mask, uint32_t *__restrict__ queue,
     uint32_t *__restrict__ qpoly, unsigned int *__restrict__ qcount, int *__restrict__ err)
@@ -410,6 +516,16 @@ __global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBl
                 const bool whole = gs >= a && gs + kSlice <= b;
                 if (pi.status != PIP_OK) {
                     ragged_slice_empty<PPL>(gs, a, b, lane, mask);
+                } else if (EXACT) {
+                    const int4 *irow = ipad + (size_t)h.j * kPadStride;
+                    const bool poly_small = fmaxf(fmaxf(-pi.bbox[0], -pi.bbox[1]), fmaxf(pi.bbox[2], pi.bbox[3])) <=
+                                            (float)(1 << 22);
+                    if (whole)
+                        ragged_slice_exact<PPL, false>(cs, irow, pi.n, poly_small, rows, pts, gs, a, b, lane, mask,
+                                                       vec_store);
+                    else
+                        ragged_slice_exact<PPL, true>(cs, irow, pi.n, poly_small, rows, pts, gs, a, b, lane, mask,
+                                                      vec_store);
                 } else if (whole) {
                     if (pi.ox == 0.f && pi.oy == 0.f)
                         ragged_slice<PPL, INT, false, false>(cs, pi.n, 0.f, 0.f, pi.beta0, pi.beta1, rows, pts, gs,

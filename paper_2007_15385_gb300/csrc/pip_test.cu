@@ -63,7 +63,7 @@ struct BatchVariant {
 constexpr BatchVariant kBatchVariants[] = {{16, 3}, {16, 2}, {12, 3}, {12, 4}};
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-template <int PPL, int STAGES, bool INT>
+template <int PPL, int STAGES, bool INT, bool EXACT>
 cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
                                   uint32_t *mask, cudaStream_t s)
 {
@@ -74,28 +74,30 @@ cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t 
         poffs, t->P, C::kTile, t->d_items, (RaggedItem *)t->d_ritems, mask);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    auto k = ragged_tma_kernel<PPL, STAGES, INT>;
+    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRaggedThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     if (per_sm > 2) per_sm = 2;
-    k<<<per_sm * t->num_sms, kRaggedThreads, C::kSmem, s>>>(t->d_poly, t->d_coefp, pts,
+    // the exact path stages the float32 integer edge rows in the coefficient rows' place
+    const float4 *rows = EXACT ? t->d_fpad : t->d_coefp;
+    k<<<per_sm * t->num_sms, kRaggedThreads, C::kSmem, s>>>(t->d_poly, rows, t->d_ipad, pts,
                                                             (const RaggedItem *)t->d_ritems, t->d_items, t->P,
                                                             t->d_work, mask, t->d_queue, t->d_keys, t->d_qcount,
                                                             t->d_error);
     return cudaGetLastError();
 }
 
-template <bool INT>
+template <bool INT, bool EXACT>
 cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
                               uint32_t *mask, cudaStream_t s)
 {
     switch (t->batch_variant) {
-    case 1: return launch_ragged_tma_one<16, 2, INT>(t, pts, M, poffs, mask, s);
-    case 2: return launch_ragged_tma_one<12, 3, INT>(t, pts, M, poffs, mask, s);
-    case 3: return launch_ragged_tma_one<12, 4, INT>(t, pts, M, poffs, mask, s);
-    default: return launch_ragged_tma_one<16, 3, INT>(t, pts, M, poffs, mask, s);
+    case 1: return launch_ragged_tma_one<16, 2, INT, EXACT>(t, pts, M, poffs, mask, s);
+    case 2: return launch_ragged_tma_one<12, 3, INT, EXACT>(t, pts, M, poffs, mask, s);
+    case 3: return launch_ragged_tma_one<12, 4, INT, EXACT>(t, pts, M, poffs, mask, s);
+    default: return launch_ragged_tma_one<16, 3, INT, EXACT>(t, pts, M, poffs, mask, s);
     }
 }
 
@@ -103,11 +105,14 @@ template <int PPL, int STAGES>
 cudaError_t set_ragged_attr()
 {
     const int bytes = (int)RaggedCfg<PPL, STAGES>::kSmem;
-    cudaError_t e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, false>,
+    cudaError_t e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, false, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes);
+        e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, true, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
@@ -476,9 +481,18 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
             PIP_CUDA_TRY(cudaMemsetAsync(t->d_qcount, 0, sizeof(unsigned int), s));
             return PIP_OK;
         }
+        if (v16 && ints && t->vdtype == PIP_I32) {
+            // integer polygons and points: uncertain points decided exactly in
+            // the bulk kernel, nothing queued, no refine launch
+            e = launch_ragged_tma<true, true>(t, d_points, num_points, d_point_offsets, mask, s);
+            if (e != cudaSuccess) return PIP_E_CUDA;
+            timing_mark(t, 1, s);
+            timing_mark(t, 2, s);
+            return PIP_OK;
+        }
         if (v16)  // bulk copies want a 16-byte aligned point array
-            e = ints ? launch_ragged_tma<true>(t, d_points, num_points, d_point_offsets, mask, s)
-                     : launch_ragged_tma<false>(t, d_points, num_points, d_point_offsets, mask, s);
+            e = ints ? launch_ragged_tma<true, false>(t, d_points, num_points, d_point_offsets, mask, s)
+                     : launch_ragged_tma<false, false>(t, d_points, num_points, d_point_offsets, mask, s);
         else
             e = ints ? launch_ragged<true, false>(t, d_points, num_points, d_point_offsets, mask, s)
                      : launch_ragged<false, false>(t, d_points, num_points, d_point_offsets, mask, s);

@@ -282,10 +282,17 @@ def test_all_pairs_mask_only():
 
 def test_integer_hulls_small():
     w = wl.integer_hulls(seed=16, num_polygons=48, points_per_polygon=3000)
+    want = oracle_own(w)
+    # 16-byte aligned points: decided exactly in the batch kernel, nothing refined
     got, _, refine, st = run_test(w)
     assert st == B.PIP_OK
-    assert_same(got, oracle_own(w), "integer hulls")
-    # on-edge and one-off points dominate the refine queue
+    assert_same(got, want, "integer hulls, exact batch kernel")
+    assert refine == 0
+    # 8-byte aligned points: float32 filter, then the int64 refine, where the
+    # on-edge and one-off points dominate the queue
+    got, _, refine, st = run_test(w, points_offset=1)
+    assert st == B.PIP_OK
+    assert_same(got, want, "integer hulls, filter and refine")
     assert refine > 0.2 * w.num_points
 
 
@@ -318,9 +325,13 @@ def test_ragged_integer_points_at_the_int32_limits():
     voffs = np.array([0, 4, 7], np.int32)
     poffs = np.array([0, len(pts_sq), len(pts)], np.int64)
     w = wl.Workload("int_limits", verts, voffs, pts, poffs)
-    got, _, refine, st = run_test(w)
+    want = oracle_own(w)
+    got, _, refine, st = run_test(w)  # exact in the batch kernel
+    assert st == B.PIP_OK and refine == 0
+    assert_same(got, want, "int32 limits, exact batch")
+    got, _, refine, st = run_test(w, points_offset=1)  # filter and refine
     assert st == B.PIP_OK and refine > 1000
-    assert_same(got, oracle_own(w), "int32 limits, batch")
+    assert_same(got, want, "int32 limits, filter and refine")
 
 
 @pytest.mark.parametrize("shape", ["footprint", "needle"])
