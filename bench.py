@@ -257,6 +257,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"],
                     help="reference: the CPU oracle timed on bounded samples of the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing on the host")
+    ap.add_argument("--calls-only", action="store_true",
+                    help="with --workload: prepare, then only W + K calls of the workload's main call "
+                         "(no tuning, graphs, comparators or oracle; a small target for profilers)")
     ap.add_argument("--headline-only", action="store_true",
                     help="time only the headline step (no per-workload objects)")
     ap.add_argument("--no-comparators", action="store_true",
@@ -806,6 +809,34 @@ def bench_workload(name: str, B, wl, dev, stream, steps: int, warmup: int, fma_p
     return out
 
 
+def run_calls_only(args, B, wl, dev, stream):
+    """--calls-only: the workload's main call W + K times after its prepare,
+    nothing else on the GPU; prints the mean time of the K timed calls."""
+    gen = getattr(wl, args.workload)
+    w = gen(num_polygons=args.polygons) if args.polygons > 0 and args.workload in (
+        "gis_batch", "gis_all_pairs", "integer_hulls") else gen()
+    import torch
+    v = torch.from_numpy(w.vertices).to(dev)
+    p = torch.from_numpy(w.points).to(dev)
+    if args.workload == "footprint_trajectory":
+        poses = torch.from_numpy(w.extra["poses"]).to(dev)
+        ws = torch.empty(B.pip_penalty_workspace_bytes(len(w.vertices), len(poses), w.num_points),
+                         dtype=torch.uint8, device=dev)
+        call = lambda: B.pip_penalty_backward(v, poses, p, w.extra["tau"], workspace=ws)
+    else:
+        vo = torch.from_numpy(w.vertex_offsets).to(dev)
+        po = torch.from_numpy(w.point_offsets).to(dev) if w.point_offsets is not None else None
+        t = B.pip_prepare(v, vo, max_points=w.num_points)
+        mode = B.PIP_MASK | (B.PIP_FIRST_HIT if args.workload == "gis_all_pairs" else 0)
+        mask = torch.empty((w.num_points + 31) // 32, dtype=torch.int32, device=dev)
+        hit = torch.empty(w.num_points, dtype=torch.int32, device=dev) if mode & B.PIP_FIRST_HIT else None
+        call = lambda: B.pip_test(t, p, po, mode=mode, mask=mask, first_hit=hit)
+    ms = time_steps(call, args.steps, args.warmup, stream)
+    print(json.dumps({"workload": args.workload, "calls_only": True, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_call": ms}))
+    return 0
+
+
 def run_other(args):
     """One JSON line for a workload other than the headline (same metric and unit)."""
     import torch
@@ -816,6 +847,8 @@ def run_other(args):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
+    if args.calls_only:
+        return run_calls_only(args, B, wl, dev, stream)
     fma_peak = measure_fma_peak(B, dev, stream)
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
