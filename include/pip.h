@@ -226,8 +226,22 @@ const char *pip_status_string(pip_status s);
  * Same-chip comparators (the paper's reference tests, Sec. 2.1-2.2, and the
  * unbatched fp64 form of Alg. 5).  Single polygon or own-polygon batch
  * (d_point_offsets as in pip_test; NULL needs num_polygons == 1), mask
- * output as in pip_test.  They are NOT exact: each decides in its own
- * precision, as the paper's listings do.
+ * output as in pip_test, float polygons and float points only (integer
+ * tables return PIP_E_INVALID_ARG).  They are NOT exact: each decides in its
+ * own precision, as the paper's listings do.
+ *
+ * They run in the Voronoi test's own frame, so that the methods differ only
+ * in their per-edge arithmetic: with one polygon and 16-byte aligned points,
+ * sign of offset and ray crossing take the pipelined single-polygon kernel
+ * (edges as launch parameters, bulk-copy ring, ballot packing); an own-polygon
+ * batch takes the pipelined batch kernel with the offsets read on the device
+ * (no host synchronisation, graph-capturable) and needs 16-byte aligned
+ * points (PIP_E_INVALID_ARG otherwise).  The fp64 form of one polygon, and
+ * one polygon's unaligned points, take a register-streaming kernel.  Calls on
+ * the same tables must not overlap each other or pip_test (they share the
+ * work-item table).  Edge k's LHS - RHS = q_y dV_x - q_x dV_y - RHS is formed
+ * as one two-FMA affine form of the point, from dV and RHS rounded to float32
+ * at pip_prepare.
  * ------------------------------------------------------------------------ */
 
 /* Alg. 2 (sign of offset) in float32: inside when every edge's

@@ -160,25 +160,25 @@ pip_status run_cmp(const pip_tables *t, const float *d_points, int64_t M, const 
         return cudaGetLastError();
     };
     if (d_point_offsets == nullptr) {
+        // one polygon: sign of offset and ray crossing through the pipelined
+        // single-polygon kernel (constant-bank edges, bulk-copy ring, ballot
+        // packing: the Voronoi kernel's frame) when the points allow bulk
+        // copies; the fp64 form and unaligned points take the register kernel
+        if (OP != kVoronoiFp64 && v16 && t->have_host_poly) {
+            PIP_CUDA_TRY(launch_cmp_stream(t, d_points, M, d_mask, OP == kSignOfOffset ? 1 : 2, s));
+            return PIP_OK;
+        }
         PIP_CUDA_TRY(launch(0, 0, M, hi_last));
         return PIP_OK;
     }
-    // own-polygon batch, one launch per polygon: the offsets come to the host
-    int64_t *h = (int64_t *)malloc(sizeof(int64_t) * (size_t)(t->P + 1));
-    if (h == nullptr) return PIP_E_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess ||
-        cudaMemcpy(h, d_point_offsets, sizeof(int64_t) * (size_t)(t->P + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
-        free(h);
-        return PIP_E_CUDA;
-    }
-    pip_status out = PIP_OK;
-    if (h[0] != 0 || h[t->P] != M) out = PIP_E_INVALID_ARG;
-    for (int j = 0; j < t->P && out == PIP_OK; ++j) {
-        if (h[j + 1] < h[j]) { out = PIP_E_INVALID_ARG; break; }
-        if (launch(j, h[j], h[j + 1], j == t->P - 1 ? hi_last : h[j + 1]) != cudaSuccess) out = PIP_E_CUDA;
-    }
-    free(h);
-    return out;
+    // own-polygon batch: the pipelined batch kernel's schedule, offsets read on
+    // the device (one sequence of launches, no host synchronisation)
+    if (!v16) return PIP_E_INVALID_ARG;
+    if (!aligned(d_point_offsets, 8)) return PIP_E_INVALID_ARG;
+    if (M > t->capacity) return PIP_E_CAPACITY;
+    PIP_CUDA_TRY(launch_ragged_cmp(t, d_points, M, d_point_offsets, d_mask,
+                                   OP == kSignOfOffset ? 1 : OP == kRayCrossing ? 2 : 3, s));
+    return PIP_OK;
 }
 
 }  // namespace

@@ -95,6 +95,11 @@ struct pip_tables {
                                  // zero past n; null for float ones
     float4 *d_fpad;              // [P][kPadStride] integer polygons: (a_x, a_y, e_x, e_y) in float32, a = v_{k-1},
                                  // e the oriented edge, zero past n; null for float ones
+    // comparators (float polygons only; null for integer ones), padded like d_coefp:
+    float4 *d_cmp_sign;          // [P][kPadStride] Alg. 2: (dV_y, -dV_x, -RHS, 0), LHS - RHS = t - x w_x - y w_y
+    float4 *d_cmp_ray;           // [P][2 kPadStride] Alg. 1, per edge (s dV_y, -s dV_x, -s RHS, 0) and
+                                 // (y_{k-1}, y_k, 0, 0), s = +1 going up, -1 otherwise; NaN past n
+    double2 *d_cmp_g64;          // [P][kPadStride] fp64 Alg. 5: p_k for k < n, p0 in the last slot
     pip::PolyInfo *d_poly;
     uint32_t *d_queue;
     uint32_t *d_keys;            // [max_points] all-pairs candidate keys
@@ -113,6 +118,8 @@ struct pip_tables {
     int have_host_poly;
     pip::PolyInfo h_poly;
     float4 h_coef[pip::kMaxEdges];
+    float4 h_cmp_sign[pip::kMaxEdges];
+    float4 h_cmp_ray[2 * pip::kMaxEdges];
     // pip_timing: event triples (before bulk, after bulk, after refine)
     int timing;
     int timed_calls;
@@ -154,6 +161,15 @@ cudaError_t launch_stream_pipelined(const pip_tables *t, const void *pts, bool i
 cudaError_t launch_stream_pipelined_i32(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask,
                                         cudaStream_t s);
 cudaError_t stream_kernels_setup_i32();
+// pip_stream.cu: the comparators (op 1 = sign of offset, 2 = ray crossing) on
+// one float polygon through the pipelined single-polygon kernel
+cudaError_t launch_cmp_stream(const pip_tables *t, const float *pts, int64_t M, uint32_t *mask, int op,
+                              cudaStream_t s);
+// pip_test.cu: the comparators (op 1 sign of offset, 2 ray crossing, 3 fp64
+// Alg. 5) on an own-polygon batch through the pipelined batch kernel
+// (16-byte aligned float points; the offsets stay on the device)
+cudaError_t launch_ragged_cmp(const pip_tables *t, const float *pts, int64_t M, const int64_t *poffs, uint32_t *mask,
+                              int op, cudaStream_t s);
 }  // namespace pip
 
 namespace pip {

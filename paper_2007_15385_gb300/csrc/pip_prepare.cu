@@ -47,6 +47,49 @@ __global__ void pad_coef_kernel(const PolyInfo *__restrict__ poly, const float4 
     }
 }
 
+// One warp per float polygon: the comparators' rows.  Edge k joins
+// u = v_{k-1} and v = v_k; dV = v - u and RHS = u_y dV_x - u_x dV_y in float32,
+// as the listings form them (Alg. 1, Alg. 2), so that
+// LHS - RHS = q_y dV_x - q_x dV_y - RHS is the two-FMA affine form the
+// Voronoi kernels evaluate, t - x w_x - y w_y with (w_x, w_y, t) =
+// (dV_y, -dV_x, -RHS).  Rows past n are NaN: the comparators' min and max
+// ignore NaN, and a NaN edge is never in range.  Invalid polygons are
+// skipped by their status.  The fp64 row holds the generators p_k and, in the
+// last slot, p0.
+__global__ void cmp_pad_kernel(const PolyInfo *__restrict__ poly, const float2 *__restrict__ verts,
+                               const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab, int P,
+                               float4 *__restrict__ sign_rows, float4 *__restrict__ ray_rows,
+                               double2 *__restrict__ g64_rows)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    if (j >= P) return;
+    const PolyInfo pi = poly[j];
+    const int n = pi.status == PIP_OK ? pi.n : 0;
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int k = lane; k < kPadStride; k += 32) {
+        float4 sg = make_float4(0.f, 0.f, qnan, 0.f);
+        float4 r0 = make_float4(0.f, 0.f, qnan, 0.f), r1 = make_float4(qnan, qnan, 0.f, 0.f);
+        double2 g = make_double2(0.0, 0.0);
+        if (k < n) {
+            const int km = k == 0 ? n - 1 : k - 1;
+            const float2 u = verts[pi.voff + km], v = verts[pi.voff + k];
+            const float dvx = v.x - u.x, dvy = v.y - u.y;
+            const float rhs = fmaf(u.y, dvx, -(u.x * dvy));
+            sg = make_float4(dvy, -dvx, -rhs, 0.f);
+            const float s = v.y > u.y ? 1.f : -1.f;  // going up
+            r0 = make_float4(s * dvy, -s * dvx, -s * rhs, 0.f);
+            r1 = make_float4(u.y, v.y, 0.f, 0.f);
+            g = gktab[pi.voff + k];
+        }
+        if (k == kPadStride - 1 && n > 0) g = g0tab[j];
+        sign_rows[(size_t)j * kPadStride + k] = sg;
+        ray_rows[(size_t)j * 2 * kPadStride + 2 * k] = r0;
+        ray_rows[(size_t)j * 2 * kPadStride + 2 * k + 1] = r1;
+        g64_rows[(size_t)j * kPadStride + k] = g;
+    }
+}
+
 }  // namespace
 
 namespace pip {
@@ -107,6 +150,9 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     const size_t o_iedge = take(vdtype == PIP_I32 ? V * sizeof(int4) : 0);
     const size_t o_ipad = take(vdtype == PIP_I32 ? P * kPadStride * sizeof(int4) : 0);
     const size_t o_fpad = take(vdtype == PIP_I32 ? P * kPadStride * sizeof(float4) : 0);
+    const size_t o_csign = take(vdtype == PIP_F32 ? P * kPadStride * sizeof(float4) : 0);
+    const size_t o_cray = take(vdtype == PIP_F32 ? P * 2 * kPadStride * sizeof(float4) : 0);
+    const size_t o_cg64 = take(vdtype == PIP_F32 ? P * kPadStride * sizeof(double2) : 0);
     const size_t o_poly = take(P * sizeof(PolyInfo));
     const size_t o_items = take((P + 1) * sizeof(int64_t));
     // items of the pipelined own-polygon kernel: a range [a, b) touches at most
@@ -136,6 +182,9 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
     t->d_iedge = vdtype == PIP_I32 ? (int4 *)(b + o_iedge) : nullptr;
     t->d_ipad = vdtype == PIP_I32 ? (int4 *)(b + o_ipad) : nullptr;
     t->d_fpad = vdtype == PIP_I32 ? (float4 *)(b + o_fpad) : nullptr;
+    t->d_cmp_sign = vdtype == PIP_F32 ? (float4 *)(b + o_csign) : nullptr;
+    t->d_cmp_ray = vdtype == PIP_F32 ? (float4 *)(b + o_cray) : nullptr;
+    t->d_cmp_g64 = vdtype == PIP_F32 ? (double2 *)(b + o_cg64) : nullptr;
     t->d_poly = (PolyInfo *)(b + o_poly);
     t->d_items = (int64_t *)(b + o_items);
     t->d_ritems = (void *)(b + o_ritems);
@@ -174,6 +223,9 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
                                                        t->d_iedge);
             int_pad_kernel<<<blocks, threads, 0, s>>>(t->d_poly, (const int2 *)t->d_verts, num_polygons,
                                                       t->d_ipad, t->d_fpad);
+        } else {
+            cmp_pad_kernel<<<blocks, threads, 0, s>>>(t->d_poly, (const float2 *)t->d_verts, t->d_g0, t->d_gk,
+                                                      num_polygons, t->d_cmp_sign, t->d_cmp_ray, t->d_cmp_g64);
         }
         e = cudaGetLastError();
     }
@@ -185,6 +237,12 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
         if (e == cudaSuccess) {
             const int n = total_vertices < kMaxEdges ? total_vertices : kMaxEdges;
             e = cudaMemcpy(t->h_coef, t->d_coef, (size_t)n * sizeof(float4), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && t->d_cmp_sign) {
+                e = cudaMemcpy(t->h_cmp_sign, t->d_cmp_sign, (size_t)n * sizeof(float4), cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(t->h_cmp_ray, t->d_cmp_ray, (size_t)2 * n * sizeof(float4),
+                                   cudaMemcpyDeviceToHost);
+            }
         }
         if (e == cudaSuccess) t->have_host_poly = 1;
     }

@@ -42,13 +42,16 @@ struct RaggedHeader {
 constexpr int kRaggedWarps = 7;  // consumer warps
 constexpr int kRaggedThreads = (kRaggedWarps + 1) * 32;
 
-template <int PPL, int STAGES>
+// ROWS: 16-byte entries per edge of the staged polygon row (2 for the ray
+// comparator, 1 otherwise).
+template <int PPL, int STAGES, int ROWS = 1>
 struct RaggedCfg {
     static constexpr int kSlice = 32 * PPL;
     static constexpr int kTile = kRaggedWarps * kSlice;  // points per item, at most
     static constexpr size_t kPtsBytes = (size_t)kTile * 8;
     static constexpr size_t kCoefOff = kPtsBytes;
-    static constexpr size_t kInfoOff = kCoefOff + (size_t)kPadStride * sizeof(float4);
+    static constexpr size_t kRowBytes = (size_t)ROWS * kPadStride * sizeof(float4);
+    static constexpr size_t kInfoOff = kCoefOff + kRowBytes;
     static constexpr size_t kHdrOff = kInfoOff + sizeof(PolyInfo);
     static constexpr size_t kStageBytes = (kHdrOff + sizeof(RaggedHeader) + 127) & ~(size_t)127;
     static constexpr size_t kBarOff = STAGES * kStageBytes;
@@ -394,6 +397,102 @@ __device__ __forceinline__ void ragged_slice_exact(const float4 *fs, const int4 
     ragged_store_words<PPL, TAIL>(w_in, gs, a, b, lane, mask, vec_store);
 }
 
+// What a batch slice decides: the Voronoi test (filter, or exact for integer
+// inputs) or one of the comparators in the same frame (float32 points and
+// polygons): sign of offset (Alg. 2), ray crossing (Alg. 1) and the literal
+// fp64 Alg. 5.
+constexpr int kRagVoronoi = 0, kRagSign = 1, kRagRay = 2, kRagFp64 = 3;
+
+// A comparator slice, float32 points in absolute coordinates as in the
+// listings.  Rows: sign of offset (w_x, w_y, t, 0) per edge with
+// LHS - RHS = t - x w_x - y w_y; ray (w, t times the going-up sign) and
+// (y_{k-1}, y_k); fp64 p_k per edge and p0 in the last slot.  Padding is NaN
+// (sign, ray), so the polygon's whole rows run in groups of four edges.
+template <int OP, int PPL, bool TAIL>
+__device__ __forceinline__ void ragged_slice_cmp(const float4 *cs, int n, const unsigned char *rows,
+                                                 const void *__restrict__ pts, int64_t gs, int64_t a, int64_t b,
+                                                 int lane, uint32_t *__restrict__ mask, bool vec_store)
+{
+    float xs[PPL], ys[PPL];
+    bool valid[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        const int r = 32 * q + lane;
+        const int64_t p = gs + r;
+        float x = 0.f, y = 0.f;
+        valid[q] = !TAIL || (p >= a && p < b);
+        if (valid[q]) {
+            if (TAIL && p == b - 1 && (b & 1)) {
+                x = ((const float *)pts)[2 * p];
+                y = ((const float *)pts)[2 * p + 1];
+            } else {
+                const float2 v = ((const float2 *)rows)[r];
+                x = v.x;
+                y = v.y;
+            }
+        }
+        xs[q] = x;
+        ys[q] = y;
+    }
+    const int npad = (n + 3) & ~3;
+    bool in[PPL];
+    if (OP == kRagSign) {
+        float mn[PPL], mx[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) mn[q] = mx[q] = __int_as_float(0x7fc00000);
+        for (int k = 0; k < npad; k += 4) {
+            const float4 c0 = cs[k], c1 = cs[k + 1], c2 = cs[k + 2], c3 = cs[k + 3];
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                const float v0 = fmaf(-xs[q], c0.x, fmaf(-ys[q], c0.y, c0.z));
+                const float v1 = fmaf(-xs[q], c1.x, fmaf(-ys[q], c1.y, c1.z));
+                const float v2 = fmaf(-xs[q], c2.x, fmaf(-ys[q], c2.y, c2.z));
+                const float v3 = fmaf(-xs[q], c3.x, fmaf(-ys[q], c3.y, c3.z));
+                mn[q] = fmin3(fmin3(mn[q], v0, v1), v2, v3);
+                mx[q] = fmax3(fmax3(mx[q], v0, v1), v2, v3);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) in[q] = mn[q] >= 0.f || mx[q] < 0.f;
+    } else if (OP == kRagRay) {
+        uint32_t par[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) par[q] = 0u;
+        for (int k = 0; k < npad; k += 2) {
+            const float4 c0 = cs[2 * k], e0 = cs[2 * k + 1], c1 = cs[2 * k + 2], e1 = cs[2 * k + 3];
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                const float v0 = fmaf(-xs[q], c0.x, fmaf(-ys[q], c0.y, c0.z));
+                const float v1 = fmaf(-xs[q], c1.x, fmaf(-ys[q], c1.y, c1.z));
+                const bool s0 = (e0.y > ys[q]) != (e0.x > ys[q]);
+                const bool s1 = (e1.y > ys[q]) != (e1.x > ys[q]);
+                par[q] ^= (uint32_t)(s0 && v0 > 0.f) ^ (uint32_t)(s1 && v1 > 0.f);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) in[q] = par[q] != 0u;
+    } else {
+        const double2 *g = (const double2 *)cs;
+        const double2 g0 = g[kPadStride - 1];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            const double x = xs[q], y = ys[q];
+            const double d0x = x - g0.x, d0y = y - g0.y;
+            const double M0 = d0x * d0x + d0y * d0y;
+            bool ok = true;
+            for (int k = 0; k < n; ++k) {
+                const double dx = x - g[k].x, dy = y - g[k].y;
+                ok &= M0 <= dx * dx + dy * dy;
+            }
+            in[q] = ok;
+        }
+    }
+    uint32_t w_in[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) w_in[q] = __ballot_sync(0xffffffffu, valid[q] && in[q]);
+    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, lane, mask, vec_store);
+}
+
 // A polygon that failed validation contains no point: its words are zero.
 template <int PPL>
 __device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_t b, int lane,
@@ -408,16 +507,18 @@ __device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_
 // EXACT (integer polygons and points): `coefp` is the table of the polygons'
 // float32 edge rows (a_x, a_y, e_x, e_y) and every point is decided exactly in
 // the consumers (nothing is queued); `ipad` holds the int64 rows for points or
-// polygons beyond +-2^22.
-template <int PPL, int STAGES, bool INT, bool EXACT>
-__global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBlocks) ragged_tma_kernel(
+// polygons beyond +-2^22.  OP other than kRagVoronoi: a comparator, `coefp`
+// its row table (float polygons and points), nothing queued.
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi>
+__global__ void __launch_bounds__(kRaggedThreads,
+                                  RaggedCfg<PPL, STAGES, OP == kRagRay ? 2 : 1>::kMinBlocks) ragged_tma_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, const int4 *__restrict__ ipad,
     const void *__restrict__ pts,
     const RaggedItem *__restrict__ items, const int64_t *__restrict__ prefix, int P,
     unsigned int *__restrict__ counters, uint32_t *__restrict__ mask, uint32_t *__restrict__ queue,
     uint32_t *__restrict__ qpoly, unsigned int *__restrict__ qcount, int *__restrict__ err)
 {
-    using C = RaggedCfg<PPL, STAGES>;
+    using C = RaggedCfg<PPL, STAGES, OP == kRagRay ? 2 : 1>;
     constexpr int kSlice = C::kSlice;
     constexpr int kTile = C::kTile;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -474,10 +575,10 @@ __global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBl
                 h->hi = ci.hi;
                 h->rot = rot;
                 rot = (rot + (ci.hi - 1) / kSlice - ci.lo / kSlice + 1) % kRaggedWarps;
-                const uint32_t cbytes = (uint32_t)(kPadStride * sizeof(float4));
+                const uint32_t cbytes = (uint32_t)C::kRowBytes;
                 mbar_arrive_expect_tx(&full[s], pbytes + cbytes + (uint32_t)sizeof(PolyInfo));
                 if (pbytes) bulk_copy_g2s(st + (sa - c0) * 8, (const char *)pts + sa * 8, pbytes, &full[s]);
-                bulk_copy_g2s(st + C::kCoefOff, coefp + (size_t)ci.j * kPadStride, cbytes, &full[s]);
+                bulk_copy_g2s(st + C::kCoefOff, (const char *)coefp + (size_t)ci.j * C::kRowBytes, cbytes, &full[s]);
                 bulk_copy_g2s(st + C::kInfoOff, poly + ci.j, (uint32_t)sizeof(PolyInfo), &full[s]);
                 cur = nxt;
                 nxt = after;
@@ -516,6 +617,9 @@ __global__ void __launch_bounds__(kRaggedThreads, RaggedCfg<PPL, STAGES>::kMinBl
                 const bool whole = gs >= a && gs + kSlice <= b;
                 if (pi.status != PIP_OK) {
                     ragged_slice_empty<PPL>(gs, a, b, lane, mask);
+                } else if (OP != kRagVoronoi) {
+                    if (whole) ragged_slice_cmp<OP, PPL, false>(cs, pi.n, rows, pts, gs, a, b, lane, mask, vec_store);
+                    else ragged_slice_cmp<OP, PPL, true>(cs, pi.n, rows, pts, gs, a, b, lane, mask, vec_store);
                 } else if (EXACT) {
                     const int4 *irow = ipad + (size_t)h.j * kPadStride;
                     const bool poly_small = fmaxf(fmaxf(-pi.bbox[0], -pi.bbox[1]), fmaxf(pi.bbox[2], pi.bbox[3])) <=

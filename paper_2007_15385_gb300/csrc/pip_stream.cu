@@ -1,8 +1,88 @@
 // pip_stream.cu -- the pipelined single-polygon test for float32 points, the
 // dispatch by point type, and the tile-shape API and autotuner.
+#include <limits>
+
 #include "pip_stream_launch.cuh"
 
 using namespace pip;
+
+namespace {
+
+// The comparators run at one tile shape, the headline's default (16 points
+// per lane, 3 stages).
+constexpr int kCmpPPL = 16, kCmpStages = 3;
+
+template <int NE, int OP>
+cudaError_t launch_cmp_one(const pip_tables *t, const float *pts, int64_t M, uint32_t *mask, cudaStream_t s)
+{
+    using C = StreamCfg<kCmpPPL, kCmpStages>;
+    auto k = stream_tma_kernel<NE, kCmpPPL, kCmpStages, false, OP>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStreamThreads, C::kSmem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    const int64_t tiles = (M + C::kTile - 1) / C::kTile;
+    const int blocks = (int)max((int64_t)1, min((int64_t)per_sm * t->num_sms, tiles));
+    StreamPoly sp;
+    const PolyInfo &hp = t->h_poly;
+    sp.ox = sp.oy = sp.b0 = sp.b1 = 0.f;
+    sp.ok = hp.status == PIP_OK;
+    sp.n = sp.ok ? hp.n : 1;
+    sp.pad0 = sp.pad1 = 0;
+    const float qnan = std::numeric_limits<float>::quiet_NaN();
+    for (int e = 0; e < kParamEdges; ++e) {
+        float4 c = make_float4(0.f, 0.f, qnan, 0.f), y = make_float4(qnan, qnan, 0.f, 0.f);
+        if (sp.ok && e < sp.n) {
+            c = OP == kTmaSign ? t->h_cmp_sign[e] : t->h_cmp_ray[2 * e];
+            if (OP == kTmaRay) y = t->h_cmp_ray[2 * e + 1];
+        }
+        sp.wx[e] = c.x;
+        sp.wy[e] = c.y;
+        sp.t[e] = c.z;
+        sp.y0[e] = y.x;
+        sp.y1[e] = y.y;
+    }
+    const float4 *rows = OP == kTmaSign ? t->d_cmp_sign : t->d_cmp_ray;
+    k<<<blocks, kStreamThreads, C::kSmem, s>>>(sp, t->d_poly, rows, t->d_g0, t->d_gk, t->d_verts, t->vdtype, pts,
+                                               M, mask, t->d_queue, (StreamCounters *)t->d_stream_ctr, t->d_qcount,
+                                               t->d_error);
+    return cudaGetLastError();
+}
+
+template <int OP>
+cudaError_t launch_cmp_ne(const pip_tables *t, const float *pts, int64_t M, uint32_t *mask, cudaStream_t s)
+{
+    const int n = t->V;
+    if (n <= 4) return launch_cmp_one<4, OP>(t, pts, M, mask, s);
+    if (n <= 8) return launch_cmp_one<8, OP>(t, pts, M, mask, s);
+    if (n <= 12) return launch_cmp_one<12, OP>(t, pts, M, mask, s);
+    if (n <= 16) return launch_cmp_one<16, OP>(t, pts, M, mask, s);
+    return launch_cmp_one<0, OP>(t, pts, M, mask, s);
+}
+
+template <int OP>
+cudaError_t set_cmp_attr()
+{
+    const int bytes = (int)StreamCfg<kCmpPPL, kCmpStages>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(stream_tma_kernel<4, kCmpPPL, kCmpStages, false, OP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stream_tma_kernel<8, kCmpPPL, kCmpStages, false, OP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stream_tma_kernel<12, kCmpPPL, kCmpStages, false, OP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stream_tma_kernel<16, kCmpPPL, kCmpStages, false, OP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stream_tma_kernel<0, kCmpPPL, kCmpStages, false, OP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+}  // namespace
 
 namespace pip {
 
@@ -10,7 +90,15 @@ cudaError_t stream_kernels_setup()
 {
     cudaError_t e = setup_stream_type<false>();
     if (e == cudaSuccess) e = stream_kernels_setup_i32();
+    if (e == cudaSuccess) e = set_cmp_attr<kTmaSign>();
+    if (e == cudaSuccess) e = set_cmp_attr<kTmaRay>();
     return e;
+}
+
+cudaError_t launch_cmp_stream(const pip_tables *t, const float *pts, int64_t M, uint32_t *mask, int op,
+                              cudaStream_t s)
+{
+    return op == kTmaSign ? launch_cmp_ne<kTmaSign>(t, pts, M, mask, s) : launch_cmp_ne<kTmaRay>(t, pts, M, mask, s);
 }
 
 int stream_variant_count() { return kNumStreamVariants; }

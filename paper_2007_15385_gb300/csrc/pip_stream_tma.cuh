@@ -36,7 +36,7 @@ struct StreamCfg {
     static constexpr int kTile = kConsumerWarps * 32 * PPL;  // points per stage
     static constexpr size_t kStageBytes = (size_t)kTile * 8;
     static constexpr size_t kCoefOff = STAGES * kStageBytes;
-    static constexpr int kCoef = kMaxEdges + 4;  // float4 (w_x, w_y, t, 0), padded to 4
+    static constexpr int kCoef = 2 * (kMaxEdges + 4);  // float4 (w_x, w_y, t, 0), padded to 4; ray: two per edge
     static constexpr size_t kBarOff = kCoefOff + (size_t)kCoef * 16;
     static constexpr size_t kSmem = kBarOff + 2 * STAGES * sizeof(uint64_t);
     // two CTAs per SM (16 consumer warps, <= 112 registers a thread) when the
@@ -45,14 +45,24 @@ struct StreamCfg {
     static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
 };
 
+// What the per-edge term decides: the Voronoi test (Alg. 5, Eq. 11
+// expanded), or the paper's comparators run in the same frame, sign of offset
+// (Alg. 2) and ray crossing (Alg. 1), whose LHS - RHS is the same two-FMA
+// affine form with other coefficients.
+constexpr int kTmaVoronoi = 0, kTmaSign = 1, kTmaRay = 2;
+
 // The polygon as launch parameters: read from the constant bank by the
-// FMAs themselves (no registers, no loads).  Edges past n carry w = 0,
-// t = +inf; an invalid polygon carries one edge with t = -inf.
+// FMAs themselves (no registers, no loads).  Voronoi: edges past n carry
+// w = 0, t = +inf, an invalid polygon one edge with t = -inf.  Comparators:
+// (w_x, w_y, t) = (dV_y, -dV_x, -RHS) (ray: times the edge's going-up sign),
+// y0 / y1 the edge's end ordinates (ray only); edges past n and an invalid
+// polygon carry t = NaN, y0 = y1 = NaN.
 constexpr int kParamEdges = 16;
 struct StreamPoly {
     float ox, oy, b0, b1;
     int n, ok, pad0, pad1;
     float wx[kParamEdges], wy[kParamEdges], t[kParamEdges];
+    float y0[kParamEdges], y1[kParamEdges];
 };
 
 struct SliceCtx {
@@ -179,9 +189,124 @@ __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned
     }
 }
 
+// The comparators' slice (float32 points, absolute coordinates as in the
+// listings): v_k = LHS_k - RHS_k = t_k - x w_kx - y w_ky per edge.  Sign of
+// offset: inside when every D_k = (v_k < 0) is the same, i.e. min v >= 0 or
+// max v < 0 (NaN padding ignored by the plain min / max; a NaN point is
+// outside).  Ray crossing: edge k crosses the +x ray when its ends straddle y
+// (y_{k-1} > y differs from y_k > y) and the signed v_k > 0; an odd count is
+// inside.  NE > 0: coefficients from the launch parameters, else from shared
+// memory (ray: (w_x, w_y, t, 0) and (y0, y1, 0, 0) per edge).
+template <int OP, int NE, int PPL, bool TAIL>
+__device__ __forceinline__ void consume_slice_cmp(const SliceCtx &cx, const unsigned char *stage,
+                                                  const void *__restrict__ pts, int64_t M, int64_t wfirst, int lane,
+                                                  uint32_t *__restrict__ mask, bool vec_store)
+{
+    const int nvalid = TAIL ? (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst)) : 32 * PPL;
+    const StreamPoly &sp = *cx.sp;
+    float xs[PPL], ys[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        const int r = 32 * q + lane;
+        float x = 0.f, y = 0.f;
+        if (!TAIL || r < nvalid) {
+            if (TAIL && wfirst + r == M - 1 && (M & 1)) {
+                x = ((const float *)pts)[2 * (M - 1)];
+                y = ((const float *)pts)[2 * (M - 1) + 1];
+            } else {
+                const float2 v = ((const float2 *)stage)[r];
+                x = v.x;
+                y = v.y;
+            }
+        }
+        xs[q] = x;
+        ys[q] = y;
+    }
+    bool in[PPL];
+    if (OP == kTmaSign) {
+        float mn[PPL], mx[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            mn[q] = __int_as_float(0x7fc00000);
+            mx[q] = __int_as_float(0x7fc00000);
+        }
+        if (NE > 0) {
+#pragma unroll
+            for (int k = 0; k < (NE > 0 ? NE : 2); k += 2) {
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    const float v0 = fmaf(-xs[q], sp.wx[k], fmaf(-ys[q], sp.wy[k], sp.t[k]));
+                    const float v1 = fmaf(-xs[q], sp.wx[k + 1], fmaf(-ys[q], sp.wy[k + 1], sp.t[k + 1]));
+                    mn[q] = fmin3(mn[q], v0, v1);
+                    mx[q] = fmax3(mx[q], v0, v1);
+                }
+            }
+        } else {
+            for (int k = 0; k < cx.npad; ++k) {
+                const float4 c = cx.cs[k];
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    const float v = fmaf(-xs[q], c.x, fmaf(-ys[q], c.y, c.z));
+                    mn[q] = fminf(mn[q], v);
+                    mx[q] = fmaxf(mx[q], v);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) in[q] = mn[q] >= 0.f || mx[q] < 0.f;
+    } else {
+        uint32_t par[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) par[q] = 0u;
+        if (NE > 0) {
+#pragma unroll
+            for (int k = 0; k < (NE > 0 ? NE : 1); ++k) {
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    const float v = fmaf(-xs[q], sp.wx[k], fmaf(-ys[q], sp.wy[k], sp.t[k]));
+                    const bool straddle = (sp.y1[k] > ys[q]) != (sp.y0[k] > ys[q]);
+                    par[q] ^= (uint32_t)(straddle && v > 0.f);
+                }
+            }
+        } else {
+            for (int k = 0; k < cx.npad; ++k) {
+                const float4 c = cx.cs[2 * k], e = cx.cs[2 * k + 1];
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    const float v = fmaf(-xs[q], c.x, fmaf(-ys[q], c.y, c.z));
+                    const bool straddle = (e.y > ys[q]) != (e.x > ys[q]);
+                    par[q] ^= (uint32_t)(straddle && v > 0.f);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) in[q] = par[q] != 0u;
+    }
+    uint32_t w_in[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) w_in[q] = __ballot_sync(0xffffffffu, in[q] && (!TAIL || 32 * q + lane < nvalid));
+    uint32_t *mw = mask + (wfirst >> 5);
+    if (!TAIL && vec_store && (PPL % 4) == 0) {
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < PPL; q += 4)
+                *(uint4 *)(mw + q) = make_uint4(w_in[q], w_in[q + 1], w_in[q + 2], w_in[q + 3]);
+        }
+    } else {
+        const int nw = (nvalid + 31) >> 5;
+        uint32_t myword = 0;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            if (lane == q) myword = w_in[q];
+        if (lane < nw) mw[lane] = myword;
+    }
+}
+
 // NE > 0: the polygon has at most NE edges and the coefficients live in
 // registers; NE == 0: any edge count, coefficients read from shared memory.
-template <int NE, int PPL, int STAGES, bool INT>
+// OP: the Voronoi test (with its exact refine) or a comparator (no refine;
+// `coef` is then the polygon's comparator row, padded with NaN).
+template <int NE, int PPL, int STAGES, bool INT, int OP = kTmaVoronoi>
 __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBlocks) stream_tma_kernel(
     const __grid_constant__ StreamPoly sp, const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
     const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab,
@@ -200,7 +325,11 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = sp.ok ? sp.n : 1;
     const int npad = (n + 3) & ~3;
-    if (NE == 0) {
+    if (NE == 0 && OP != kTmaVoronoi) {
+        // comparator rows (already padded with NaN past n; ray: two per edge)
+        const int rows = (OP == kTmaRay ? 2 : 1) * npad;
+        for (int k = tid; k < rows; k += blockDim.x) cs[k] = coef[k];  // an invalid polygon: all NaN
+    } else if (NE == 0) {
         // more edges than the parameter block holds: stage them in shared memory
         const PolyInfo pi = poly[0];
         for (int k = tid; k < npad; k += blockDim.x) {
@@ -273,7 +402,12 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
             if (!mbar_wait(&full[s], fphase, err)) break;
             const unsigned char *stage = smem + (size_t)s * C::kStageBytes + (size_t)warp * 32 * PPL * 8;
             const bool whole = wfirst + 32 * PPL <= whole_end;
-            if (whole) {
+            if (OP != kTmaVoronoi) {
+                if (whole)
+                    consume_slice_cmp<OP, NE, PPL, false>(cx, stage, pts, M, wfirst, lane, mask, vec_store);
+                else
+                    consume_slice_cmp<OP, NE, PPL, true>(cx, stage, pts, M, wfirst, lane, mask, vec_store);
+            } else if (whole) {
                 if (center)
                     consume_slice<NE, PPL, INT, true, false>(cx, stage, pts, M, wfirst, lane, mask,
                                                                    vec_store, myqueue, &s_refined);
@@ -293,6 +427,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
         }
     }
     __syncthreads();
+    if (OP != kTmaVoronoi) return;  // the comparators decide in float32, as the listings do
     // exact decision of this CTA's queued points, one warp per point (every
     // warp of the CTA, the producer's included); their mask words were
     // written above with the bit clear

@@ -63,25 +63,29 @@ struct BatchVariant {
 constexpr BatchVariant kBatchVariants[] = {{16, 3}, {16, 2}, {12, 3}, {12, 4}};
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-template <int PPL, int STAGES, bool INT, bool EXACT>
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi>
 cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
                                   uint32_t *mask, cudaStream_t s)
 {
-    using C = RaggedCfg<PPL, STAGES>;
+    using C = RaggedCfg<PPL, STAGES, OP == kRagRay ? 2 : 1>;
     ragged_items_kernel<<<1, 1024, 0, s>>>(poffs, t->P, M, C::kTile, t->d_items, t->ritems_cap, t->d_work,
                                            t->d_qcount, t->d_worst);
     ragged_fill_kernel<<<(unsigned)std::min((t->P + 7) / 8, t->num_sms * 8), 256, 0, s>>>(
         poffs, t->P, C::kTile, t->d_items, (RaggedItem *)t->d_ritems, mask);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT>;
+    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRaggedThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     if (per_sm > 2) per_sm = 2;
-    // the exact path stages the float32 integer edge rows in the coefficient rows' place
-    const float4 *rows = EXACT ? t->d_fpad : t->d_coefp;
+    // the exact path stages the float32 integer edge rows in the coefficient
+    // rows' place, a comparator its own rows
+    const float4 *rows = OP == kRagSign ? t->d_cmp_sign
+                         : OP == kRagRay ? t->d_cmp_ray
+                         : OP == kRagFp64 ? (const float4 *)t->d_cmp_g64
+                         : EXACT ? t->d_fpad : t->d_coefp;
     k<<<per_sm * t->num_sms, kRaggedThreads, C::kSmem, s>>>(t->d_poly, rows, t->d_ipad, pts,
                                                             (const RaggedItem *)t->d_ritems, t->d_items, t->P,
                                                             t->d_work, mask, t->d_queue, t->d_keys, t->d_qcount,
@@ -99,6 +103,13 @@ cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, c
     case 3: return launch_ragged_tma_one<12, 4, INT, EXACT>(t, pts, M, poffs, mask, s);
     default: return launch_ragged_tma_one<16, 3, INT, EXACT>(t, pts, M, poffs, mask, s);
     }
+}
+
+template <int OP>
+cudaError_t set_ragged_cmp_attr()
+{
+    return cudaFuncSetAttribute(ragged_tma_kernel<16, 3, false, false, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RaggedCfg<16, 3, OP == kRagRay ? 2 : 1>::kSmem);
 }
 
 template <int PPL, int STAGES>
@@ -419,7 +430,19 @@ cudaError_t ragged_kernels_setup()
     if (e == cudaSuccess) e = set_ragged_attr<16, 2>();
     if (e == cudaSuccess) e = set_ragged_attr<12, 3>();
     if (e == cudaSuccess) e = set_ragged_attr<12, 4>();
+    if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagSign>();
+    if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagRay>();
+    if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagFp64>();
     return e;
+}
+
+cudaError_t launch_ragged_cmp(const pip_tables *t, const float *pts, int64_t M, const int64_t *poffs, uint32_t *mask,
+                              int op, cudaStream_t s)
+{
+    // one tile shape: 16 points per lane, 3 stages
+    if (op == kRagSign) return launch_ragged_tma_one<16, 3, false, false, kRagSign>(t, pts, M, poffs, mask, s);
+    if (op == kRagRay) return launch_ragged_tma_one<16, 3, false, false, kRagRay>(t, pts, M, poffs, mask, s);
+    return launch_ragged_tma_one<16, 3, false, false, kRagFp64>(t, pts, M, poffs, mask, s);
 }
 
 cudaError_t allpairs_setup()

@@ -133,6 +133,14 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return d;
 }
 
+// max of three (a NaN operand is ignored unless all are NaN)
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // min of three; NaN if any operand is NaN
 __device__ __forceinline__ float fmin3_nan(float a, float b, float c)
 {

@@ -699,6 +699,52 @@ def test_comparators_ragged_match_the_oracle_listings():
     t.close()
 
 
+@pytest.mark.parametrize("n", [3, 8, 13, 16, 40])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_comparators_every_edge_count_and_alignment(n, offset):
+    """Sign of offset, ray crossing and fp64 Alg. 5 on one polygon: the
+    pipelined kernel's register variants (up to 16 edges), its shared-memory
+    variant (40 edges), and the register-streaming kernel for points that are
+    8 but not 16 bytes aligned; element by element against the oracle."""
+    w = wl.unit_circle_octagon(seed=200 + n, m=70_001, n=n)
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    flat = np.zeros(2 * (w.num_points + offset), np.float32)
+    flat[2 * offset:] = w.points.reshape(-1)
+    p = torch.from_numpy(flat).to(dev())[2 * offset:]
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    got = {fn.__name__: B.unpack_mask(fn(t, p), w.num_points).cpu().numpy() for fn in COMPARATORS}
+    left_out = _comparator_checks(got, w.vertices, w.points)
+    assert left_out < w.num_points // 100
+    t.close()
+
+
+def test_comparators_ragged_replay_from_a_cuda_graph():
+    w = wl.gis_batch(seed=23, num_polygons=40, m_range=(0, 3000))
+    v = torch.from_numpy(w.vertices).to(dev())
+    vo = torch.from_numpy(w.vertex_offsets).to(dev())
+    p = torch.from_numpy(w.points).to(dev())
+    po = torch.from_numpy(w.point_offsets).to(dev())
+    t = B.pip_prepare(v, vo, max_points=w.num_points)
+    for fn in COMPARATORS:
+        eager = B.unpack_mask(fn(t, p, po), w.num_points).cpu().numpy()
+        out = torch.zeros((w.num_points + 31) // 32, dtype=torch.int32, device=dev())
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn(t, p, po, mask=out)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn(t, p, po, mask=out)
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert_same(B.unpack_mask(out, w.num_points).cpu().numpy(), eager, fn.__name__ + " graph replay")
+    t.close()
+
+
 def test_repeated_calls_reset_the_refine_queue():
     w = wl.integer_hulls(seed=22, num_polygons=8, points_per_polygon=1000)
     v = torch.from_numpy(w.vertices).to(dev())
