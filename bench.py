@@ -387,6 +387,20 @@ def main():
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / e2e_steps
     e2e_value = whole_job_rate(tests_per_step, world, e2e_ms)
     h2d_bytes, d2h_bytes = int(p_host.numel() * 4), int(mask_host.numel() * 4)
+    # the host link alone: the same bytes as one plain host-to-device copy
+    # (pinned memory, copy engine), the floor of the end-to-end step
+    for _ in range(2):
+        p.copy_(p_host, non_blocking=True)
+    torch.cuda.synchronize()
+    l0 = torch.cuda.Event(enable_timing=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    l0.record(stream)
+    for _ in range(5):
+        p.copy_(p_host, non_blocking=True)
+    l1.record(stream)
+    torch.cuda.synchronize()
+    link_ms = l0.elapsed_time(l1) / 5
+    link_gbs = h2d_bytes / (link_ms * 1e-3) / 1e9
 
     # same-chip comparators on the same workload (Alg. 2, Alg. 1, plain fp64 Alg. 5)
     comparators = {}
@@ -451,7 +465,11 @@ def main():
                        "stream_variant": variant},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes},
+                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
+                    "call": "pip_test_host (C ABI: pieces copied on the tables' copy stream, "
+                            "tested and read back on the caller's stream)",
+                    "host_link": {"h2d_gbs": link_gbs, "copy_ms": link_ms,
+                                  "note": "one plain %d-byte pinned host-to-device copy, the same run" % h2d_bytes}},
             "gpu_launches": calls_launches * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

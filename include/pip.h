@@ -131,6 +131,33 @@ pip_status pip_test(const pip_tables *t, const void *d_points, pip_dtype pdtype,
                     uint32_t *d_mask, int32_t *d_first_hit, void *stream);
 
 /*
+ * pip_test_host -- pip_test on host buffers: the paper has no counterpart to
+ * this call; it serves callers whose points live in host memory.  Mask only,
+ * with d_point_offsets NULL (one polygon, or "inside any polygon" for
+ * several).  The points move to the caller's device staging buffer in
+ * `pieces` pieces (1..64, each a multiple of 128 points but the last) on a
+ * copy stream the tables own; piece i is tested on `stream` once its copy has
+ * landed, and its mask words go back to h_mask on `stream`, so that copying
+ * piece i + 1 overlaps testing and reading back piece i.  One cudaMemcpyAsync
+ * per piece and direction.
+ *
+ *   h_points     host, [num_points][2] of `pdtype`; page-locked
+ *                (cudaHostAlloc / cudaHostRegister) for the copies to overlap
+ *   d_points     device staging, [num_points][2], 16-byte aligned
+ *   d_mask       device staging, uint32 [ceil(num_points / 32)], 16-byte aligned
+ *   h_mask       host, uint32 [ceil(num_points / 32)], the result
+ *   num_points   0 <= num_points <= max_points of pip_prepare
+ *
+ * Enqueues only: h_mask is complete once `stream` has finished the work
+ * queued before return (synchronize it).  The first call on a set of tables
+ * creates its copy stream and events (released by pip_destroy), so make it
+ * before any stream capture.  Calls on the same tables must not overlap.
+ * Returns PIP_OK, PIP_E_INVALID_ARG, PIP_E_CAPACITY or PIP_E_CUDA.
+ */
+pip_status pip_test_host(pip_tables *t, const void *h_points, pip_dtype pdtype, int64_t num_points, void *d_points,
+                         uint32_t *d_mask, uint32_t *h_mask, int32_t pieces, void *stream);
+
+/*
  * pip_margin -- signed Voronoi margin in length units.  Edge k is the set of
  * points equidistant from p0 and p_k (Eq. 2); the signed distance of x from
  * that bisector is (|x - p0|^2 - |x - p_k|^2) / (2 |p_k - p0|), and the margin

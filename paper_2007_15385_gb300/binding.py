@@ -56,6 +56,7 @@ SIGNATURES = {
     "pip_stream_variant_count": (_I32, []),
     "pip_selftest_wait_timeout": (_INT, [_P, _P, _I64, _P]),
     "pip_fma_peak": (_INT, [_I32, _I32, _P, _I64, _P, ctypes.POINTER(_I64)]),
+    "pip_test_host": (_INT, [_P, _P, _INT, _I64, _P, _P, _P, _I32, _P]),
     "pip_raster_workspace_bytes": (ctypes.c_size_t, [_I32, _I32, _I32]),
     "pip_rasterize": (_INT, [_P, _I32, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              _P, _P, _P, ctypes.c_size_t, _P]),
@@ -338,33 +339,24 @@ def unpack_mask(mask: torch.Tensor, num_points: int) -> torch.Tensor:
 
 def pip_test_host(tables: Tables, points_host: torch.Tensor, device_points: torch.Tensor,
                   device_mask: torch.Tensor, mask_host: torch.Tensor, stream=None, chunks: int = 8):
-    """End-to-end call on host buffers (one polygon or all pairs, mask only): pinned host
-    points -> device, pip_test, mask -> pinned host, in `chunks` pieces so that the copy of
-    one piece overlaps the test and the read-back of the previous one.  The caller provides
-    the device staging buffers, so nothing is allocated per call.  Pieces start at multiples
-    of 128 points (whole, 16-byte aligned mask words) and are tested in order on `stream`
-    (they share the tables' refine queue); the copies run on a second stream."""
-    s = stream if stream is not None else torch.cuda.current_stream()
+    """End-to-end call on host buffers through the C ABI's pip_test_host (one polygon or all
+    pairs, mask only): pinned host points -> device staging buffer -> pip_test -> pinned host
+    mask, in `chunks` pieces so that the copy of one piece overlaps the test and the read-back
+    of the previous one.  The caller provides the staging buffers; nothing is allocated per
+    call.  Returns mask_host (complete once the stream has run)."""
+    for t_, nm in ((points_host, "points_host"), (mask_host, "mask_host")):
+        if t_.is_cuda or not t_.is_contiguous():
+            raise ValueError("%s must be a contiguous host tensor" % nm)
+    _dev(device_points, "device_points")
+    _dev(device_mask, "device_mask")
     M = points_host.numel() // 2
-    piece = max(128, -(-M // max(1, int(chunks)) // 128) * 128)
-    cs = getattr(tables, "_copy_stream", None)
-    if cs is None or cs.device != device_points.device:
-        cs = torch.cuda.Stream(device=device_points.device)
-        tables._copy_stream = cs
-    cs.wait_stream(s)  # the staging buffers are free once earlier work on `stream` is done
-    hp = points_host.view(-1)
-    dp = device_points.view(-1)
-    for a in range(0, M, piece):
-        b = min(M, a + piece)
-        with torch.cuda.stream(cs):
-            dp[2 * a:2 * b].copy_(hp[2 * a:2 * b], non_blocking=True)
-            ready = torch.cuda.Event()
-            ready.record(cs)
-        s.wait_event(ready)
-        with torch.cuda.stream(s):
-            w0, w1 = a // 32, (b + 31) // 32
-            pip_test(tables, dp[2 * a:2 * b], mask=device_mask[w0:w1], stream=s)
-            mask_host[w0:w1].copy_(device_mask[w0:w1], non_blocking=True)
+    if device_points.numel() < 2 * M or device_mask.numel() < (M + 31) // 32 or mask_host.numel() < (M + 31) // 32:
+        raise ValueError("staging or result buffers are smaller than the points need")
+    if device_points.dtype != points_host.dtype:
+        raise TypeError("device_points must have the host points' dtype")
+    _check(lib().pip_test_host(tables, points_host.data_ptr(), _dtype_code(points_host), M,
+                               device_points.data_ptr(), device_mask.data_ptr(), mask_host.data_ptr(),
+                               int(chunks), _stream(stream)), "pip_test_host")
     return mask_host
 
 

@@ -120,6 +120,10 @@ struct pip_tables {
     float4 h_coef[pip::kMaxEdges];
     float4 h_cmp_sign[pip::kMaxEdges];
     float4 h_cmp_ray[2 * pip::kMaxEdges];
+    // pip_test_host: a copy stream and events, created at its first call
+    cudaStream_t host_copy_stream;
+    cudaEvent_t host_events[65];
+    int host_ready;
     // pip_timing: event triples (before bulk, after bulk, after refine)
     int timing;
     int timed_calls;

@@ -266,6 +266,10 @@ void pip_destroy(pip_tables *t)
         for (int i = 0; i < 3 * kTimingSlots; ++i) cudaEventDestroy(t->events[i]);
         free(t->events);
     }
+    if (t->host_ready) {
+        for (int i = 0; i < 65; ++i) cudaEventDestroy(t->host_events[i]);
+        cudaStreamDestroy(t->host_copy_stream);
+    }
     free(t);
 }
 

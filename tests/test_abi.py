@@ -97,6 +97,11 @@ def test_host_argument_checks_of_the_other_entry_points(lib):
     assert lib.pip_penalty_forward(None, 12, None, 4, None, 10, 0.05, None, None, 0, None) == B.PIP_E_INVALID_ARG
     assert lib.pip_penalty_backward(None, 12, None, 4, None, 10, 0.05, None, None, None, None, 0,
                                     None) == B.PIP_E_INVALID_ARG
+    # the host-buffer call and the FMA calibration kernel refuse bad handles and sizes
+    assert lib.pip_test_host(None, None, 0, 10, None, None, None, 8, None) == B.PIP_E_INVALID_ARG
+    fm = ctypes.c_int64(0)
+    assert lib.pip_fma_peak(0, 1, None, 0, None, ctypes.byref(fm)) == B.PIP_E_INVALID_ARG
+    assert lib.pip_fma_peak(8, 0, None, 0, None, ctypes.byref(fm)) == B.PIP_E_INVALID_ARG
     # the allocation-free one-polygon call checks its arguments first
     assert lib.pip_test_single_noalloc(None, 0, 8, None, 0, 10, None, None, None) == B.PIP_E_INVALID_ARG
     assert lib.pip_test_single_noalloc(8, 5, 8, 8, 0, 10, 8, None, None) == B.PIP_E_INVALID_ARG  # bad dtype

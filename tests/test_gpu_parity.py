@@ -384,6 +384,27 @@ def test_host_call_in_pieces_matches_the_oracle(chunks):
     t.close()
 
 
+def test_host_call_all_pairs_and_integer_points():
+    """pip_test_host through the C ABI for several polygons (inside any) and
+    for integer points, against the oracle."""
+    w = wl.gis_all_pairs(num_polygons=30, m=50_011)
+    ints = wl.integer_hulls(seed=24, num_polygons=1, points_per_polygon=40_000)
+    for v, vo, pts, want in ((w.vertices, w.vertex_offsets, w.points,
+                              (oracle.first_hit_exact(w.vertices, w.vertex_offsets, w.points) >= 0).astype(np.uint8)),
+                             (ints.vertices, ints.vertex_offsets, ints.points, oracle_own(ints))):
+        t = B.pip_prepare(torch.from_numpy(v).to(dev()), torch.from_numpy(vo).to(dev()), max_points=len(pts))
+        ph = torch.from_numpy(pts).pin_memory()
+        pd = torch.empty(pts.shape, dtype=ph.dtype, device=dev())
+        nw = (len(pts) + 31) // 32
+        md = torch.empty(nw, dtype=torch.int32, device=dev())
+        mh = torch.full((nw,), -1, dtype=torch.int32).pin_memory()
+        B.pip_test_host(t, ph, pd, md, mh, chunks=5)
+        torch.cuda.synchronize()
+        got = np.unpackbits(mh.numpy().view(np.uint8), bitorder="little")[:len(pts)]
+        assert_same(got, want, "host call")
+        t.close()
+
+
 def test_nonfinite_points_are_outside():
     v = wl.regular_polygon(6, 1.0).astype(np.float32)
     pts = np.array([[0, 0], [np.nan, 0], [0, np.inf], [-np.inf, np.inf], [np.inf, np.inf],
