@@ -268,7 +268,8 @@ def main():
                     help="points of the workload (default the full 2^26; smaller only for profiling)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "gis_batch", "gis_all_pairs", "integer_hulls",
-                             "footprint_trajectory", "unit_circle_octagon", "paper_sweep", "gis_raster"],
+                             "footprint_trajectory", "unit_circle_octagon", "paper_sweep", "gis_raster",
+                             "inner_generator"],
                     help="which workload to time (the default is the headline)")
     ap.add_argument("--polygons", type=int, default=0,
                     help="number of polygons of the batch workloads (0: the workload's own; "
@@ -286,6 +287,8 @@ def main():
         return run_sweep(args)
     if args.workload == "gis_raster":
         return run_raster(args)
+    if args.workload == "inner_generator":
+        return run_inner_generator(args)
     if args.workload != WORKLOAD:
         return run_other(args)
 
@@ -420,6 +423,12 @@ def main():
             cms = c0.elapsed_time(c1) / reps
             comparators[name] = {"ms": cms, "Gtests_per_s": tests_per_step / (cms * 1e-3) / 1e9}
 
+    # the sequential test's early break (PIP_EARLY_EXIT, warp-uniform): same
+    # results, less work, reported as an effective rate apart from the value
+    ems = time_steps(lambda: B.pip_test(t, p, mode=B.PIP_MASK | B.PIP_EARLY_EXIT, mask=mask), 20, 3, stream)
+    early_exit = {"ms_per_step": ems, "effective_Gtests_per_s": tests_per_step / (ems * 1e-3) / 1e9,
+                  "note": "PIP_EARLY_EXIT: a warp stops once all its points are decided outside"}
+
     # the signed margin (pip_margin) on the same points, apart from the step:
     # 8 B read + 4 B written per point, against the same HBM peak
     marg = torch.empty(M, dtype=torch.float32, device=dev)
@@ -479,6 +488,7 @@ def main():
                          "bytes_per_launch": bytes_per_launch, "kernel_ms": bulk_avg_ms,
                          "refine_kernel_ms": refine_ms / max(1, calls)},
             "comparators": comparators,
+            "early_exit": early_exit,
             "margin": margin,
             "cpu_baseline": cpu,
         }
@@ -612,6 +622,67 @@ def run_sweep(args):
             "config": {"workload": "paper_sweep", "edges": "3..15", "polygon": "n sorted random angles on the unit circle",
                        "points": "uniform in [-1.5, 1.5]^2", "value": "geometric mean over n of Voronoi Gtests/s, 10^6-point batches"},
             "clocks": clk, "gpu_launches": 13 * 2 * 4 * (reps + 3), "sweep": rows}
+    print(json.dumps(line))
+    return 0
+
+
+def run_inner_generator(args):
+    """The inner-generator study (Sec. 3: any interior point may be p0): the
+    float32 filter's refine fraction and the call's time with the centroid
+    (Eq. 3-4), the vertex mean and the Chebyshev centre (largest inscribed
+    circle, by LP on the host) as p0, on the first 1,024 GIS polygons with
+    their points and on the 1,024 integer hulls with their points as float32
+    (so that the filter, not the exact integer path, decides them)."""
+    import torch
+
+    from paper_2007_15385_gb300 import binding as B
+    from paper_2007_15385_gb300 import workloads as wl
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    cases = {"gis_batch_1024": wl.gis_batch(num_polygons=args.polygons or 1024),
+             "integer_hulls_f32_points": wl.integer_hulls(num_polygons=args.polygons or 1024)}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    study = {}
+    for cname, w in cases.items():
+        v = torch.from_numpy(w.vertices).to(dev)
+        vo = torch.from_numpy(w.vertex_offsets).to(dev)
+        p = torch.from_numpy(w.points.astype(np.float32)).to(dev)
+        po = torch.from_numpy(w.point_offsets).to(dev)
+        mask = torch.empty((w.num_points + 31) // 32, dtype=torch.int32, device=dev)
+        t0 = time.perf_counter()
+        cheb = torch.from_numpy(wl.chebyshev_centres(w.vertices, w.vertex_offsets)).to(dev)
+        lp_s = time.perf_counter() - t0
+        rows = {}
+        for kind, code, given in (("centroid", B.PIP_P0_CENTROID, None),
+                                  ("vertex_mean", B.PIP_P0_VERTEX_MEAN, None),
+                                  ("chebyshev_centre", B.PIP_P0_GIVEN, cheb)):
+            t = B.pip_prepare_p0(v, vo, w.num_points, code, given)
+            st, _ = B.pip_get_status(t)
+            call = lambda: B.pip_test(t, p, po, mask=mask)
+            ms = time_steps(call, args.steps, args.warmup, stream)
+            B.pip_timing(t, True)
+            for _ in range(args.steps):
+                call()
+            calls, bulk_ms, refine_ms = B.pip_timing_read(t)
+            B.pip_timing(t, False)
+            _, refined = B.pip_get_status(t)
+            rows[kind] = {"status": st, "ms_per_call": ms, "bulk_ms": bulk_ms / max(1, calls),
+                          "refine_ms": refine_ms / max(1, calls), "refined_points": refined,
+                          "refine_fraction": refined / w.num_points,
+                          "Gtests_per_s": w.tests() / (ms * 1e-3) / 1e9}
+            t.close()
+        study[cname] = {"num_polygons": w.num_polygons, "num_points": w.num_points, "lp_seconds": lp_s,
+                        "p0": rows}
+    clk = clocks.stop()
+    g = study["gis_batch_1024"]["p0"]["centroid"]
+    line = {"metric": METRIC, "value": g["Gtests_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": g["ms_per_call"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "inner_generator", "value": "GIS batch (1,024 polygons), centroid p0"},
+            "clocks": clk, "gpu_launches": 4 * args.steps * 6, "study": study}
     print(json.dumps(line))
     return 0
 
@@ -778,6 +849,12 @@ def bench_workload(name: str, B, wl, dev, stream, steps: int, warmup: int, fma_p
             call()
         out["graph_ms_per_step"] = time_steps(graph.replay, steps, 3, stream)
         del graph
+        if name in ("gis_batch", "unit_circle_octagon"):
+            # the early break (PIP_EARLY_EXIT): same results, less work
+            ecall = lambda: B.pip_test(t, p, po, mode=mode | B.PIP_EARLY_EXIT, mask=mask, first_hit=hit)
+            ems = time_steps(ecall, steps, 3, stream)
+            out["early_exit"] = {"ms_per_step": ems, "effective_Gtests_per_s": tests / (ems * 1e-3) / 1e9,
+                                 "note": "PIP_EARLY_EXIT: a warp stops once all its points are decided outside"}
         if name == "gis_all_pairs":
             # bounding-box cull and early stop (PIP_CULL): same results, less work;
             # reported apart as an effective rate, not as the full-work value

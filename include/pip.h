@@ -57,7 +57,7 @@ typedef enum {
 typedef enum { PIP_F32 = 0, PIP_I32 = 1 } pip_dtype;
 
 /* pip_test output selection (bit flags) */
-enum { PIP_MASK = 1, PIP_FIRST_HIT = 2, PIP_CULL = 4 };
+enum { PIP_MASK = 1, PIP_FIRST_HIT = 2, PIP_CULL = 4, PIP_EARLY_EXIT = 8 };
 
 /* Opaque: device tables built from a batch of polygons (generators,
  * coefficients, bounds, validation results) plus the refine workspace. */
@@ -93,6 +93,27 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype,
                        pip_tables **out);
 
 /*
+ * pip_prepare_p0 -- pip_prepare with another inner generator.  Any point
+ * strictly inside the polygon may serve as p0 (Sec. 3): the mirrored
+ * generators and the test's results are then the same closed-polygon
+ * membership, only the float32 coefficients and their error bound change.
+ *
+ *   p0_kind   PIP_P0_CENTROID (Eq. 3-4, what pip_prepare takes),
+ *             PIP_P0_VERTEX_MEAN (the mean of the polygon's vertices), or
+ *             PIP_P0_GIVEN (d_p0)
+ *   d_p0      device double [num_polygons][2], 16-byte aligned, absolute
+ *             coordinates; read only for PIP_P0_GIVEN (may be NULL otherwise)
+ *
+ * A p0 that is not clearly inside every edge line (or not finite) makes the
+ * polygon PIP_E_DEGENERATE, as pip_get_status reports.  Everything else as
+ * pip_prepare.
+ */
+enum { PIP_P0_CENTROID = 0, PIP_P0_VERTEX_MEAN = 1, PIP_P0_GIVEN = 2 };
+pip_status pip_prepare_p0(const void *d_vertices, pip_dtype vdtype, const int32_t *d_vertex_offsets,
+                          int32_t num_polygons, int32_t total_vertices, int64_t max_points, int32_t p0_kind,
+                          const double *d_p0, void *stream, pip_tables **out);
+
+/*
  * pip_test -- Voronoi inclusion (Alg. 5 with the squared-distance form of
  * Eq. 10-11), bit-exact against exact closed-polygon membership.
  *
@@ -112,6 +133,14 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype,
  *                     a block stops once each of its points has a candidate.
  *                     Same results, less work; not the paper's full-work
  *                     timing convention (Sec. 6.2).  Ignored otherwise.
+ *                     PIP_EARLY_EXIT may be added for one polygon or an
+ *                     own-polygon batch (16-byte aligned points): the
+ *                     sequential test's early break (Sec. 5), warp-uniform --
+ *                     edges are taken in groups of four spread around the
+ *                     polygon and a warp stops once all its points are
+ *                     decided outside.  Same results, less work; not the
+ *                     full-work convention either.  Ignored by the exact
+ *                     integer batch path and the all-pairs test.
  *   d_mask            device uint32 [ceil(num_points / 32)]; bit (i % 32) of
  *                     word (i / 32) is 1 when point i is inside its polygon
  *                     (own-polygon batch) or inside at least one polygon

@@ -29,6 +29,10 @@ PIP_I32 = 1
 PIP_MASK = 1
 PIP_FIRST_HIT = 2
 PIP_CULL = 4  # all pairs: skip polygons by bounding box, stop early (same results)
+PIP_P0_CENTROID = 0
+PIP_P0_VERTEX_MEAN = 1
+PIP_P0_GIVEN = 2
+PIP_EARLY_EXIT = 8  # one polygon / batch: warp-uniform early break over spread edges (same results)
 
 # every symbol include/pip.h declares, with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -37,6 +41,7 @@ _I64 = ctypes.c_int64
 _INT = ctypes.c_int
 SIGNATURES = {
     "pip_prepare": (_INT, [_P, _INT, _P, _I32, _I32, _I64, _P, ctypes.POINTER(_P)]),
+    "pip_prepare_p0": (_INT, [_P, _INT, _P, _I32, _I32, _I64, _I32, _P, _P, ctypes.POINTER(_P)]),
     "pip_test": (_INT, [_P, _P, _INT, _I64, _P, _INT, _P, _P, _P]),
     "pip_margin": (_INT, [_P, _P, _INT, _I64, _P, _P, _P]),
     "pip_get_status": (_INT, [_P, _P, ctypes.POINTER(_I64)]),
@@ -172,6 +177,33 @@ def pip_prepare(vertices: torch.Tensor, vertex_offsets: torch.Tensor, max_points
     _check(lib().pip_prepare(vertices.data_ptr(), _dtype_code(vertices), vertex_offsets.data_ptr(),
                              P, V, int(max_points), _stream(stream), ctypes.byref(h)), "pip_prepare")
     return Tables(h, P, V, int(max_points), vertices.device)
+
+
+def pip_prepare_p0(vertices: torch.Tensor, vertex_offsets: torch.Tensor, max_points: int, p0_kind: int,
+                   p0: torch.Tensor | None = None, stream=None) -> Tables:
+    """pip_prepare with another inner generator: PIP_P0_CENTROID, PIP_P0_VERTEX_MEAN, or
+    PIP_P0_GIVEN with p0 a float64 CUDA tensor [num_polygons, 2] of interior points."""
+    _dev(vertices, "vertices")
+    _dev(vertex_offsets, "vertex_offsets")
+    if vertex_offsets.dtype != torch.int32:
+        raise TypeError("vertex_offsets must be int32")
+    P = vertex_offsets.numel() - 1
+    V = vertices.numel() // 2
+    ptr = None
+    if p0_kind == PIP_P0_GIVEN:
+        if p0 is None:
+            raise ValueError("PIP_P0_GIVEN needs p0")
+        _dev(p0, "p0")
+        if p0.dtype != torch.float64 or p0.numel() != 2 * P or p0.device != vertices.device:
+            raise ValueError("p0 must be float64 [num_polygons, 2] on the vertices' device")
+        ptr = p0.data_ptr()
+    h = ctypes.c_void_p()
+    _check(lib().pip_prepare_p0(vertices.data_ptr(), _dtype_code(vertices), vertex_offsets.data_ptr(), P, V,
+                                int(max_points), int(p0_kind), ptr, _stream(stream), ctypes.byref(h)),
+           "pip_prepare_p0")
+    tables = Tables(h, P, V, int(max_points), vertices.device)
+    tables._keep_p0 = p0  # read by the prepare kernel, which may still be running
+    return tables
 
 
 def pip_test(tables: Tables, points: torch.Tensor, point_offsets: torch.Tensor | None = None,

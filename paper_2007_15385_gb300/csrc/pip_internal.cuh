@@ -160,9 +160,9 @@ cudaError_t ragged_kernels_setup();
 cudaError_t allpairs_setup();
 int stream_variant_count();
 // the pipelined single-polygon test (pip_stream.cu): one launch, refine inline
-cudaError_t launch_stream_pipelined(const pip_tables *t, const void *pts, bool ints, int64_t M, uint32_t *mask,
+cudaError_t launch_stream_pipelined(const pip_tables *t, const void *pts, bool ints, int64_t M, uint32_t *mask, bool early,
                                     cudaStream_t s);
-cudaError_t launch_stream_pipelined_i32(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask,
+cudaError_t launch_stream_pipelined_i32(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, bool early,
                                         cudaStream_t s);
 cudaError_t stream_kernels_setup_i32();
 // pip_stream.cu: the comparators (op 1 = sign of offset, 2 = ray crossing) on

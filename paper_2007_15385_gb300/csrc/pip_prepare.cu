@@ -112,9 +112,32 @@ pip_status check_tables(const pip_tables *t)
 
 extern "C" {
 
+static pip_status prepare_impl(const void *d_vertices, pip_dtype vdtype, const int32_t *d_vertex_offsets,
+                               int32_t num_polygons, int32_t total_vertices, int64_t max_points, int p0_kind,
+                               const double *d_p0, void *stream, pip_tables **out);
+
 pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *d_vertex_offsets,
                        int32_t num_polygons, int32_t total_vertices, int64_t max_points,
                        void *stream, pip_tables **out)
+{
+    return prepare_impl(d_vertices, vdtype, d_vertex_offsets, num_polygons, total_vertices, max_points,
+                        kP0Centroid, nullptr, stream, out);
+}
+
+pip_status pip_prepare_p0(const void *d_vertices, pip_dtype vdtype, const int32_t *d_vertex_offsets,
+                          int32_t num_polygons, int32_t total_vertices, int64_t max_points, int32_t p0_kind,
+                          const double *d_p0, void *stream, pip_tables **out)
+{
+    if (p0_kind != PIP_P0_CENTROID && p0_kind != PIP_P0_VERTEX_MEAN && p0_kind != PIP_P0_GIVEN)
+        return PIP_E_INVALID_ARG;
+    if (p0_kind == PIP_P0_GIVEN && (d_p0 == nullptr || !aligned(d_p0, 16))) return PIP_E_INVALID_ARG;
+    return prepare_impl(d_vertices, vdtype, d_vertex_offsets, num_polygons, total_vertices, max_points,
+                        p0_kind, p0_kind == PIP_P0_GIVEN ? d_p0 : nullptr, stream, out);
+}
+
+static pip_status prepare_impl(const void *d_vertices, pip_dtype vdtype, const int32_t *d_vertex_offsets,
+                               int32_t num_polygons, int32_t total_vertices, int64_t max_points, int p0_kind,
+                               const double *d_p0, void *stream, pip_tables **out)
 {
     if (out == nullptr) return PIP_E_INVALID_ARG;
     *out = nullptr;
@@ -211,7 +234,8 @@ pip_status pip_prepare(const void *d_vertices, pip_dtype vdtype, const int32_t *
         const int blocks = (int)((P * 32 + threads - 1) / threads);
         prepare_kernel<<<blocks, threads, 0, s>>>(t->d_verts, vdtype, t->d_voffs, num_polygons,
                                                   total_vertices, t->d_g0, t->d_gk, t->d_coef,
-                                                  t->d_coefn, t->d_poly, t->d_worst);
+                                                  t->d_coefn, t->d_poly, t->d_worst, p0_kind,
+                                                  (const double2 *)d_p0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

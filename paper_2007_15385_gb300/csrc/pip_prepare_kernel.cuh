@@ -45,10 +45,18 @@ __device__ __forceinline__ void load_vertex(const void *verts, int vdtype, int64
 
 __device__ __forceinline__ float round_up_f32(double v) { return __double2float_ru(v); }
 
+// p0_kind: the inner generator (any interior point serves, Sec. 3):
+// kP0Centroid the centroid of Eq. 3-4 (the paper's choice), kP0VertexMean the
+// mean of the vertices, kP0Given p0_given[j] (absolute coordinates, e.g. the
+// Chebyshev centre).  Whichever is taken must be clearly inside every edge
+// line (checked below; otherwise PIP_E_DEGENERATE).
+constexpr int kP0Centroid = 0, kP0VertexMean = 1, kP0Given = 2;
+
 __global__ void __launch_bounds__(256) prepare_kernel(
     const void *__restrict__ verts, int vdtype, const int32_t *__restrict__ voffs, int P, int V,
     double2 *__restrict__ g0_out, double2 *__restrict__ gk_out, float4 *__restrict__ coef,
-    float4 *__restrict__ coefn, PolyInfo *__restrict__ poly, int32_t *__restrict__ worst)
+    float4 *__restrict__ coefn, PolyInfo *__restrict__ poly, int32_t *__restrict__ worst,
+    int p0_kind = kP0Centroid, const double2 *__restrict__ p0_given = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int j = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -62,7 +70,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(
     if (!range_ok || n < kMinEdges || n > kMaxEdges) status = PIP_E_INVALID_ARG;
 
     double sx = 0.0, sy = 0.0;  // shift origin: vertex 0
-    double S = 0.0, Cx = 0.0, Cy = 0.0, D = 0.0;
+    double S = 0.0, Cx = 0.0, Cy = 0.0, D = 0.0, Mx = 0.0, My = 0.0;
     int wraps[2] = {0, 0};  // vertices where the edge direction turns across angle 0, ccw / cw
     float bb[4] = {INFINITY, INFINITY, -INFINITY, -INFINITY};
     bool nonfinite = false, zero_edge = false, int_bad = false, fold = false;
@@ -90,6 +98,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(
             // Eq. 3-4 in coordinates relative to v_0
             const double uxm = xm - sx, uym = ym - sy, uxk = xk - sx, uyk = yk - sy;
             const double det = uxm * uyk - uxk * uym;
+            Mx += uxk;  // vertex mean, relative to v_0
+            My += uyk;
             S += det;
             Cx += (uxm + uxk) * det;
             Cy += (uym + uyk) * det;
@@ -115,6 +125,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(
         S = warp_sum(S);
         Cx = warp_sum(Cx);
         Cy = warp_sum(Cy);
+        Mx = warp_sum(Mx);
+        My = warp_sum(My);
         wraps[0] = __reduce_add_sync(0xffffffffu, wraps[0]);
         wraps[1] = __reduce_add_sync(0xffffffffu, wraps[1]);
         D = warp_max(D);
@@ -141,8 +153,18 @@ __global__ void __launch_bounds__(256) prepare_kernel(
     const int sigma = pos ? 1 : -1;
     double g0x = 0.0, g0y = 0.0;
     if (status == PIP_OK) {
-        g0x = Cx / (3.0 * S);  // Eq. 4: sum / (6 A), 2A = S
-        g0y = Cy / (3.0 * S);
+        if (p0_kind == kP0VertexMean) {
+            g0x = Mx / n;
+            g0y = My / n;
+        } else if (p0_kind == kP0Given) {
+            const double2 q = p0_given[j];
+            g0x = q.x - sx;
+            g0y = q.y - sy;
+            if (!isfinite(g0x) || !isfinite(g0y)) status = PIP_E_DEGENERATE;
+        } else {
+            g0x = Cx / (3.0 * S);  // Eq. 4: sum / (6 A), 2A = S
+            g0y = Cy / (3.0 * S);
+        }
     }
 
     // Eq. 8 generators; the centroid must sit strictly inside every edge line

@@ -187,7 +187,10 @@ __device__ __forceinline__ void ragged_store_words(const uint32_t (&w_in)[PPL], 
 // polygon j's (TAIL: the slice is not wholly inside; the odd last point of
 // the range is not in the bulk copy and is read from global memory).  An
 // uncertain point is queued with its polygon (queue / qpoly).
-template <int PPL, bool INT, bool CENTER, bool TAIL>
+// EARLY: the warp-uniform early break (as in the single-polygon kernel): edges
+// in groups of four spread around the polygon, the warp stops once all its
+// points are decided outside (min s < -B); same decisions as full work.
+template <int PPL, bool INT, bool CENTER, bool TAIL, bool EARLY = false>
 __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, float oy, float b0, float b1,
                                              const unsigned char *rows, const void *__restrict__ pts,
                                              int64_t gs, int64_t a, int64_t b, int lane,
@@ -229,7 +232,33 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
         ys[q] = CENTER ? y - oy : y;
     }
     // m = min_k s_k (NaN-propagating): three edges, then four at a time, then the rest
-    {
+    if (EARLY) {
+        const int G = ((n + 3) & ~3) / 4;  // rows are padded with w = 0, t = +inf
+        float Bq[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            Bq[q] = fmaf(b1, fabsf(xs[q]) + fabsf(ys[q]), b0);
+            m[q] = INFINITY;
+        }
+        for (int g = 0; g < G; ++g) {
+            const float4 c0 = cs[g], c1 = cs[G + g], c2 = cs[2 * G + g], c3 = cs[3 * G + g];
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                const float s0 = fmaf(-xs[q], c0.x, fmaf(-ys[q], c0.y, c0.z));
+                const float s1 = fmaf(-xs[q], c1.x, fmaf(-ys[q], c1.y, c1.z));
+                const float s2 = fmaf(-xs[q], c2.x, fmaf(-ys[q], c2.y, c2.z));
+                const float s3 = fmaf(-xs[q], c3.x, fmaf(-ys[q], c3.y, c3.z));
+                m[q] = fmin3_nan(fmin3_nan(m[q], s0, s1), s2, s3);
+            }
+            if (g + 1 < G) {
+                bool out = true;
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) out &= m[q] < -Bq[q] || !valid[q];
+                if (__all_sync(0xffffffffu, out)) break;
+            }
+        }
+    }
+    if (!EARLY) {
         const float4 c0 = cs[0], c1 = cs[1], c2 = cs[2];
 #pragma unroll
         for (int q = 0; q < PPL; ++q)
@@ -237,7 +266,7 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
                              fmaf(-xs[q], c1.x, fmaf(-ys[q], c1.y, c1.z)),
                              fmaf(-xs[q], c2.x, fmaf(-ys[q], c2.y, c2.z)));
     }
-    int k = 3;
+    int k = EARLY ? n : 3;
     for (; k + 4 <= n; k += 4) {
         const float4 c0 = cs[k], c1 = cs[k + 1], c2 = cs[k + 2], c3 = cs[k + 3];
 #pragma unroll
@@ -249,7 +278,7 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
             m[q] = fmin3_nan(fmin3_nan(m[q], s0, s1), s2, s3);
         }
     }
-    const int rem = n - k;
+    const int rem = n - k;  // 0 in the early-exit form
     if (rem == 1) {
         const float4 c0 = cs[k];
 #pragma unroll
@@ -509,7 +538,7 @@ __device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_
 // the consumers (nothing is queued); `ipad` holds the int64 rows for points or
 // polygons beyond +-2^22.  OP other than kRagVoronoi: a comparator, `coefp`
 // its row table (float polygons and points), nothing queued.
-template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi>
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false>
 __global__ void __launch_bounds__(kRaggedThreads,
                                   RaggedCfg<PPL, STAGES, OP == kRagRay ? 2 : 1>::kMinBlocks) ragged_tma_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, const int4 *__restrict__ ipad,
@@ -632,13 +661,13 @@ __global__ void __launch_bounds__(kRaggedThreads,
                                                       vec_store);
                 } else if (whole) {
                     if (pi.ox == 0.f && pi.oy == 0.f)
-                        ragged_slice<PPL, INT, false, false>(cs, pi.n, 0.f, 0.f, pi.beta0, pi.beta1, rows, pts, gs,
+                        ragged_slice<PPL, INT, false, false, EARLY>(cs, pi.n, 0.f, 0.f, pi.beta0, pi.beta1, rows, pts, gs,
                                                              a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
                     else
-                        ragged_slice<PPL, INT, true, false>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts,
+                        ragged_slice<PPL, INT, true, false, EARLY>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts,
                                                             gs, a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
                 } else {
-                    ragged_slice<PPL, INT, true, true>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts, gs,
+                    ragged_slice<PPL, INT, true, true, EARLY>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts, gs,
                                                        a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
                 }
             }

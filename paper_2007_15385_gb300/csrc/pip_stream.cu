@@ -104,9 +104,10 @@ cudaError_t launch_cmp_stream(const pip_tables *t, const float *pts, int64_t M, 
 int stream_variant_count() { return kNumStreamVariants; }
 
 cudaError_t launch_stream_pipelined(const pip_tables *t, const void *pts, bool ints, int64_t M, uint32_t *mask,
-                                    cudaStream_t s)
+                                    bool early, cudaStream_t s)
 {
-    return ints ? launch_stream_pipelined_i32(t, pts, M, mask, s) : launch_stream_type<false>(t, pts, M, mask, s);
+    return ints ? launch_stream_pipelined_i32(t, pts, M, mask, early, s)
+                : launch_stream_type<false>(t, pts, M, mask, early, s);
 }
 
 }  // namespace pip

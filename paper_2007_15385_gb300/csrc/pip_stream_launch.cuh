@@ -20,11 +20,11 @@ struct StreamVariant {
 constexpr StreamVariant kStreamVariants[] = {{16, 3}, {16, 2}, {8, 4}, {8, 6}};
 constexpr int kNumStreamVariants = sizeof(kStreamVariants) / sizeof(kStreamVariants[0]);
 
-template <int NE, int PPL, int STAGES, bool INT>
+template <int NE, int PPL, int STAGES, bool INT, bool EARLY = false>
 cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
 {
     using C = StreamCfg<PPL, STAGES>;
-    auto k = stream_tma_kernel<NE, PPL, STAGES, INT>;
+    auto k = stream_tma_kernel<NE, PPL, STAGES, INT, kTmaVoronoi, EARLY>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStreamThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
@@ -55,33 +55,33 @@ cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint
     return cudaGetLastError();
 }
 
-template <int PPL, int STAGES, bool INT>
+template <int PPL, int STAGES, bool INT, bool EARLY = false>
 cudaError_t launch_tma_ne(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
 {
     // the polygon's edge count is known on the host from the vertex count
     const int n = t->V;
-    if (n <= 4) return launch_tma_one<4, PPL, STAGES, INT>(t, pts, M, mask, s);
-    if (n <= 8) return launch_tma_one<8, PPL, STAGES, INT>(t, pts, M, mask, s);
-    if (n <= 12) return launch_tma_one<12, PPL, STAGES, INT>(t, pts, M, mask, s);
-    if (n <= 16) return launch_tma_one<16, PPL, STAGES, INT>(t, pts, M, mask, s);
-    return launch_tma_one<0, PPL, STAGES, INT>(t, pts, M, mask, s);
+    if (n <= 4) return launch_tma_one<4, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
+    if (n <= 8) return launch_tma_one<8, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
+    if (n <= 12) return launch_tma_one<12, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
+    if (n <= 16) return launch_tma_one<16, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
+    return launch_tma_one<0, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
 }
 
-template <int NE, int PPL, int STAGES, bool INT>
+template <int NE, int PPL, int STAGES, bool INT, bool EARLY = false>
 cudaError_t set_attr_one()
 {
-    return cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, INT>,
+    return cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, INT, kTmaVoronoi, EARLY>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StreamCfg<PPL, STAGES>::kSmem);
 }
 
-template <int PPL, int STAGES, bool INT>
+template <int PPL, int STAGES, bool INT, bool EARLY = false>
 cudaError_t set_smem_attr()
 {
-    cudaError_t e = set_attr_one<4, PPL, STAGES, INT>();
-    if (e == cudaSuccess) e = set_attr_one<8, PPL, STAGES, INT>();
-    if (e == cudaSuccess) e = set_attr_one<12, PPL, STAGES, INT>();
-    if (e == cudaSuccess) e = set_attr_one<16, PPL, STAGES, INT>();
-    if (e == cudaSuccess) e = set_attr_one<0, PPL, STAGES, INT>();
+    cudaError_t e = set_attr_one<4, PPL, STAGES, INT, EARLY>();
+    if (e == cudaSuccess) e = set_attr_one<8, PPL, STAGES, INT, EARLY>();
+    if (e == cudaSuccess) e = set_attr_one<12, PPL, STAGES, INT, EARLY>();
+    if (e == cudaSuccess) e = set_attr_one<16, PPL, STAGES, INT, EARLY>();
+    if (e == cudaSuccess) e = set_attr_one<0, PPL, STAGES, INT, EARLY>();
     return e;
 }
 
@@ -100,17 +100,21 @@ cudaError_t launch_stream_tma(const pip_tables *t, const void *pts, int64_t M, u
 template <bool INT>
 cudaError_t set_all_attr()
 {
-    cudaError_t e = set_smem_attr<16, 3, INT>();
+    cudaError_t e = set_smem_attr<16, 3, INT, true>();  // the early-exit mode's one tile shape
+    if (e == cudaSuccess) e = set_smem_attr<16, 3, INT>();
     if (e == cudaSuccess) e = set_smem_attr<16, 2, INT>();
     if (e == cudaSuccess) e = set_smem_attr<8, 4, INT>();
     if (e == cudaSuccess) e = set_smem_attr<8, 6, INT>();
     return e;
 }
 
-// One point type: the pipelined kernel at the chosen tile shape.
+// One point type: the pipelined kernel at the chosen tile shape; the
+// early-exit mode at the default shape (16 points per lane, 3 stages).
 template <bool INT>
-cudaError_t launch_stream_type(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
+cudaError_t launch_stream_type(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, bool early,
+                               cudaStream_t s)
 {
+    if (early) return launch_tma_ne<16, 3, INT, true>(t, pts, M, mask, s);
     return launch_stream_tma<INT>(t, pts, M, mask, s);
 }
 

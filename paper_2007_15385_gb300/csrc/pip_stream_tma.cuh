@@ -75,7 +75,13 @@ struct SliceCtx {
 // the slice's PPL mask words, queue the uncertain points.  TAIL: the slice may
 // run past M (or hold the odd last point, which is not in the bulk copy).
 // CENTER: subtract the local origin o (false when o = (0, 0)).
-template <int NE, int PPL, bool INT, bool CENTER, bool TAIL>
+// EARLY: the early break of the sequential test (Sec. 5: stop at the first
+// edge that already decides the point), made warp-uniform.  Edges run in
+// groups of four spread around the polygon (edge i * n/4 + g of group g); after
+// each group but the last, the warp stops when every one of its points already
+// has min s < -B, i.e. is decided outside.  The full min could only be
+// smaller, so the decisions are those of the full-work test.
+template <int NE, int PPL, bool INT, bool CENTER, bool TAIL, bool EARLY = false>
 __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned char *stage,
                                               const void *__restrict__ pts, int64_t M, int64_t wfirst,
                                               int lane, uint32_t *__restrict__ mask, bool vec_store,
@@ -115,7 +121,45 @@ __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned
     }
     // m = min_k s_k, NaN-propagating so that a non-finite point stays undecided;
     // three operands per min (NE is a multiple of 4)
-    if (NE > 0) {
+    if (EARLY) {
+        float Bq[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            Bq[q] = fmaf(sp.b1, fabsf(xs[q]) + fabsf(ys[q]), sp.b0);
+            m[q] = INFINITY;
+        }
+        const int G = NE > 0 ? NE / 4 : cx.npad / 4;
+        // one group of four spread edges; true when the warp may stop
+        auto group = [&](int g) -> bool {
+            float4 c[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = i * G + g;
+                c[i] = NE > 0 ? make_float4(sp.wx[k], sp.wy[k], sp.t[k], 0.f) : cx.cs[k];
+            }
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                const float s0 = fmaf(-xs[q], c[0].x, fmaf(-ys[q], c[0].y, c[0].z));
+                const float s1 = fmaf(-xs[q], c[1].x, fmaf(-ys[q], c[1].y, c[1].z));
+                const float s2 = fmaf(-xs[q], c[2].x, fmaf(-ys[q], c[2].y, c[2].z));
+                const float s3 = fmaf(-xs[q], c[3].x, fmaf(-ys[q], c[3].y, c[3].z));
+                m[q] = fmin3_nan(fmin3_nan(m[q], s0, s1), s2, s3);
+            }
+            if (g + 1 >= G) return true;
+            bool out = true;
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) out &= m[q] < -Bq[q];
+            return __all_sync(0xffffffffu, out);
+        };
+        if (NE > 0) {
+#pragma unroll
+            for (int g = 0; g < (NE > 0 ? NE / 4 : 1); ++g)
+                if (group(g)) break;
+        } else {
+            for (int g = 0; g < G; ++g)
+                if (group(g)) break;
+        }
+    } else if (NE > 0) {
 #pragma unroll
         for (int q = 0; q < PPL; ++q)
             m[q] = fmin_nan(fmaf(-xs[q], sp.wx[0], fmaf(-ys[q], sp.wy[0], sp.t[0])),
@@ -306,7 +350,7 @@ __device__ __forceinline__ void consume_slice_cmp(const SliceCtx &cx, const unsi
 // registers; NE == 0: any edge count, coefficients read from shared memory.
 // OP: the Voronoi test (with its exact refine) or a comparator (no refine;
 // `coef` is then the polygon's comparator row, padded with NaN).
-template <int NE, int PPL, int STAGES, bool INT, int OP = kTmaVoronoi>
+template <int NE, int PPL, int STAGES, bool INT, int OP = kTmaVoronoi, bool EARLY = false>
 __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBlocks) stream_tma_kernel(
     const __grid_constant__ StreamPoly sp, const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
     const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab,
@@ -409,13 +453,13 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
                     consume_slice_cmp<OP, NE, PPL, true>(cx, stage, pts, M, wfirst, lane, mask, vec_store);
             } else if (whole) {
                 if (center)
-                    consume_slice<NE, PPL, INT, true, false>(cx, stage, pts, M, wfirst, lane, mask,
+                    consume_slice<NE, PPL, INT, true, false, EARLY>(cx, stage, pts, M, wfirst, lane, mask,
                                                                    vec_store, myqueue, &s_refined);
                 else
-                    consume_slice<NE, PPL, INT, false, false>(cx, stage, pts, M, wfirst, lane, mask,
+                    consume_slice<NE, PPL, INT, false, false, EARLY>(cx, stage, pts, M, wfirst, lane, mask,
                                                                     vec_store, myqueue, &s_refined);
             } else {
-                consume_slice<NE, PPL, INT, true, true>(cx, stage, pts, M, wfirst, lane, mask,
+                consume_slice<NE, PPL, INT, true, true, EARLY>(cx, stage, pts, M, wfirst, lane, mask,
                                                               vec_store, myqueue, &s_refined);
             }
             __syncwarp();

@@ -63,7 +63,7 @@ struct BatchVariant {
 constexpr BatchVariant kBatchVariants[] = {{16, 3}, {16, 2}, {12, 3}, {12, 4}};
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi>
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false>
 cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
                                   uint32_t *mask, cudaStream_t s)
 {
@@ -74,7 +74,7 @@ cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t 
         poffs, t->P, C::kTile, t->d_items, (RaggedItem *)t->d_ritems, mask);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP>;
+    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP, EARLY>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRaggedThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
@@ -430,6 +430,12 @@ cudaError_t ragged_kernels_setup()
     if (e == cudaSuccess) e = set_ragged_attr<16, 2>();
     if (e == cudaSuccess) e = set_ragged_attr<12, 3>();
     if (e == cudaSuccess) e = set_ragged_attr<12, 4>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tma_kernel<16, 3, false, false, kRagVoronoi, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RaggedCfg<16, 3>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ragged_tma_kernel<16, 3, true, false, kRagVoronoi, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RaggedCfg<16, 3>::kSmem);
     if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagSign>();
     if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagRay>();
     if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagFp64>();
@@ -473,8 +479,9 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     if (pdtype != PIP_F32 && pdtype != PIP_I32) return PIP_E_INVALID_ARG;
     if (num_points < 0) return PIP_E_INVALID_ARG;
     if (num_points > t->capacity) return PIP_E_CAPACITY;
-    if ((mode & ~(PIP_MASK | PIP_FIRST_HIT | PIP_CULL)) || !(mode & (PIP_MASK | PIP_FIRST_HIT)))
+    if ((mode & ~(PIP_MASK | PIP_FIRST_HIT | PIP_CULL | PIP_EARLY_EXIT)) || !(mode & (PIP_MASK | PIP_FIRST_HIT)))
         return PIP_E_INVALID_ARG;
+    const bool early = (mode & PIP_EARLY_EXIT) != 0;
     const bool want_mask = mode & PIP_MASK, want_hit = mode & PIP_FIRST_HIT;
     if (want_hit && d_point_offsets != nullptr) return PIP_E_INVALID_ARG;
     if (num_points == 0) {  // nothing to decide; the refine count of this call is 0
@@ -513,7 +520,12 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
             timing_mark(t, 2, s);
             return PIP_OK;
         }
-        if (v16)  // bulk copies want a 16-byte aligned point array
+        if (v16 && early)  // the early-exit form at the default tile shape
+            e = ints ? launch_ragged_tma_one<16, 3, true, false, kRagVoronoi, true>(t, d_points, num_points,
+                                                                                  d_point_offsets, mask, s)
+                     : launch_ragged_tma_one<16, 3, false, false, kRagVoronoi, true>(t, d_points, num_points,
+                                                                                   d_point_offsets, mask, s);
+        else if (v16)  // bulk copies want a 16-byte aligned point array
             e = ints ? launch_ragged_tma<true, false>(t, d_points, num_points, d_point_offsets, mask, s)
                      : launch_ragged_tma<false, false>(t, d_points, num_points, d_point_offsets, mask, s);
         else
@@ -522,7 +534,7 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     } else if (t->P == 1 && !want_hit && v16 && t->have_host_poly) {
         // the pipelined kernel: bulk test and exact refine in one launch
         timing_mark(t, 0, s);
-        e = launch_stream_pipelined(t, d_points, ints, num_points, mask, s);
+        e = launch_stream_pipelined(t, d_points, ints, num_points, mask, early, s);
         if (e != cudaSuccess) return PIP_E_CUDA;
         timing_mark(t, 1, s);
         timing_mark(t, 2, s);

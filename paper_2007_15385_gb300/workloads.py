@@ -290,3 +290,32 @@ def regular_polygon(n: int, r: float = 1.0, cx: float = 0.0, cy: float = 0.0,
                     phase: float = 0.0, dtype=np.float64) -> np.ndarray:
     th = phase + 2.0 * math.pi * np.arange(n) / n
     return np.stack([cx + r * np.cos(th), cy + r * np.sin(th)], axis=1).astype(dtype)
+
+
+def chebyshev_centres(vertices: np.ndarray, vertex_offsets: np.ndarray) -> np.ndarray:
+    """The centre of each convex polygon's largest inscribed circle, by a
+    small linear programme per polygon (maximise r subject to
+    a_k . x + r |a_k| <= b_k for every edge half-plane a_k . x <= b_k), as
+    float64 [P, 2].  An interior point chosen without reference to the
+    Voronoi method, for studies of the inner generator p0; solved about the
+    vertex mean so that large coordinates stay well conditioned."""
+    from scipy.optimize import linprog
+    out = np.empty((len(vertex_offsets) - 1, 2))
+    for j in range(len(vertex_offsets) - 1):
+        v = vertices[vertex_offsets[j]:vertex_offsets[j + 1]].astype(np.float64)
+        c = v.mean(axis=0)
+        scale = np.abs(v - c).max()
+        v = (v - c) / scale  # unit size: the solver's tolerances are absolute
+        u = np.roll(v, 1, axis=0)
+        e = v - u
+        orient = 1.0 if (u[:, 0] * v[:, 1] - v[:, 0] * u[:, 1]).sum() > 0 else -1.0
+        a = orient * np.stack([e[:, 1], -e[:, 0]], axis=1)
+        b = orient * (e[:, 1] * u[:, 0] - e[:, 0] * u[:, 1])
+        nrm = np.linalg.norm(a, axis=1)
+        A = np.concatenate([a / nrm[:, None], np.ones((len(a), 1))], axis=1)
+        r = linprog([0.0, 0.0, -1.0], A_ub=A, b_ub=b / nrm, bounds=[(None, None), (None, None), (0, None)],
+                    method="highs")
+        if r.status != 0:
+            raise RuntimeError("Chebyshev centre of polygon %d: %s" % (j, r.message))
+        out[j] = r.x[:2] * scale + c
+    return out

@@ -766,6 +766,85 @@ def test_comparators_ragged_replay_from_a_cuda_graph():
     t.close()
 
 
+def _early_cases():
+    yield "footprint, 12 edges", wl.vehicle_footprint(seed=50, m=1_000_003)
+    for n in (3, 5, 16, 40):
+        yield "%d-gon" % n, wl.unit_circle_octagon(seed=300 + n, m=200_001, n=n)
+    hull = wl.integer_hulls(seed=51, num_polygons=1, points_per_polygon=100_000)
+    yield "integer points, float polygon", wl.Workload("h", hull.vertices.astype(np.float32),
+                                                       hull.vertex_offsets, hull.points)
+    yield "gis batch", wl.gis_batch(seed=52, num_polygons=60, m_range=(0, 20_000))
+    yield "integer batch", wl.integer_hulls(seed=53, num_polygons=20, points_per_polygon=5_000)
+
+
+def test_early_exit_equals_full_work_and_the_oracle():
+    """PIP_EARLY_EXIT stops a warp once all its points are decided outside;
+    the masks must be those of the full-work test and of the oracle."""
+    for name, w in _early_cases():
+        v = torch.from_numpy(w.vertices).to(dev())
+        vo = torch.from_numpy(w.vertex_offsets).to(dev())
+        p = torch.from_numpy(w.points).to(dev())
+        po = torch.from_numpy(w.point_offsets).to(dev()) if w.point_offsets is not None else None
+        t = B.pip_prepare(v, vo, max_points=w.num_points)
+        full, _ = B.pip_test(t, p, po)
+        early, _ = B.pip_test(t, p, po, mode=B.PIP_MASK | B.PIP_EARLY_EXIT)
+        got_full = B.unpack_mask(full, w.num_points).cpu().numpy()
+        got_early = B.unpack_mask(early, w.num_points).cpu().numpy()
+        assert_same(got_early, got_full, name + ": early exit vs full work")
+        assert_same(got_early, oracle_own(w), name + ": early exit vs the oracle")
+        t.close()
+
+
+@pytest.mark.parametrize("kind", ["centroid", "vertex_mean", "chebyshev"])
+def test_inner_generator_choices_give_the_oracle_masks(kind):
+    """Any interior point may be p0 (Sec. 3): with the vertex mean or the
+    Chebyshev centre instead of the centroid the tables hold that p0 and its
+    mirrors (Eq. 8 about it, against the oracle's generators), and the masks
+    are still exact closed-polygon membership."""
+    for w in (wl.gis_batch(seed=54, num_polygons=40, m_range=(100, 5000)),
+              wl.integer_hulls(seed=55, num_polygons=12, points_per_polygon=4000),
+              wl.vehicle_footprint(seed=56, m=100_003)):
+        v = torch.from_numpy(w.vertices).to(dev())
+        vo = torch.from_numpy(w.vertex_offsets).to(dev())
+        if kind == "centroid":
+            want_p0 = np.stack([oracle.centroid(w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]])[1]
+                                for j in range(w.num_polygons)])
+            t = B.pip_prepare_p0(v, vo, w.num_points, B.PIP_P0_CENTROID)
+        elif kind == "vertex_mean":
+            want_p0 = np.stack([w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]].astype(np.float64).mean(0)
+                                for j in range(w.num_polygons)])
+            t = B.pip_prepare_p0(v, vo, w.num_points, B.PIP_P0_VERTEX_MEAN)
+        else:
+            want_p0 = wl.chebyshev_centres(w.vertices, w.vertex_offsets)
+            t = B.pip_prepare_p0(v, vo, w.num_points, B.PIP_P0_GIVEN, torch.from_numpy(want_p0).to(dev()))
+        st, _ = B.pip_get_status(t)
+        assert st == B.PIP_OK
+        ex = B.pip_export_tables(t)
+        g0, gk = ex["g0"], ex["gk"]
+        scale = np.abs(w.vertices.astype(np.float64)).max() + 1.0
+        assert np.abs(g0 - want_p0).max() <= 1e-12 * scale
+        for j in range(w.num_polygons):
+            vv = w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]]
+            ref = oracle.generators(vv, want_p0[j])
+            assert np.abs(gk[w.vertex_offsets[j]:w.vertex_offsets[j + 1]] - ref).max() <= 1e-10 * scale
+        p = torch.from_numpy(w.points).to(dev())
+        po = torch.from_numpy(w.point_offsets).to(dev()) if w.point_offsets is not None else None
+        mask, _ = B.pip_test(t, p, po)
+        assert_same(B.unpack_mask(mask, w.num_points).cpu().numpy(), oracle_own(w), "%s, p0 = %s" % (w.name, kind))
+        t.close()
+
+
+def test_inner_generator_outside_the_polygon_is_degenerate():
+    sq = np.array([[0, 0], [4, 0], [4, 4], [0, 4]], np.float32)
+    v = torch.from_numpy(sq).to(dev())
+    vo = torch.tensor([0, 4], dtype=torch.int32, device=dev())
+    for p0 in ([5.0, 1.0], [4.0, 2.0], [float("nan"), 1.0]):  # outside, on an edge, not finite
+        t = B.pip_prepare_p0(v, vo, 16, B.PIP_P0_GIVEN, torch.tensor([p0], dtype=torch.float64, device=dev()))
+        st, _ = B.pip_get_status(t)
+        assert st == B.PIP_E_DEGENERATE
+        t.close()
+
+
 def test_repeated_calls_reset_the_refine_queue():
     w = wl.integer_hulls(seed=22, num_polygons=8, points_per_polygon=1000)
     v = torch.from_numpy(w.vertices).to(dev())
