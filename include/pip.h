@@ -272,6 +272,18 @@ pip_status pip_autotune_batch(pip_tables *t, const void *d_points, pip_dtype pdt
                               int64_t num_points, const int64_t *d_point_offsets, uint32_t *d_mask,
                               int32_t reps, void *stream, int32_t *best_variant, float *best_ms);
 
+/*
+ * pip_set_tuning_cache -- the paper has no counterpart; a JSON file where the
+ * autotuners keep their choices.  With a path set, pip_autotune_stream and
+ * pip_autotune_batch first look up the key (kernel, GPU name, polygons,
+ * vertices, points, vertex and point types): a hit sets that tile shape and
+ * returns its recorded time without any timing run or synchronisation; a miss
+ * times the variants as usual and records the winner (the file is rewritten
+ * whole, through a temporary file and a rename).  NULL or "" turns the cache
+ * off (the default).  The path is copied; process-wide.
+ */
+pip_status pip_set_tuning_cache(const char *path);
+
 /* Number of polygons / vertices held by the tables. */
 int32_t pip_num_polygons(const pip_tables *t);
 int32_t pip_total_vertices(const pip_tables *t);

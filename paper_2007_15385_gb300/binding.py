@@ -62,6 +62,7 @@ SIGNATURES = {
     "pip_selftest_wait_timeout": (_INT, [_P, _P, _I64, _P]),
     "pip_fma_peak": (_INT, [_I32, _I32, _P, _I64, _P, ctypes.POINTER(_I64)]),
     "pip_test_host": (_INT, [_P, _P, _INT, _I64, _P, _P, _P, _I32, _P]),
+    "pip_set_tuning_cache": (_INT, [ctypes.c_char_p]),
     "pip_raster_workspace_bytes": (ctypes.c_size_t, [_I32, _I32, _I32]),
     "pip_rasterize": (_INT, [_P, _I32, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              _P, _P, _P, ctypes.c_size_t, _P]),
@@ -428,6 +429,11 @@ def pip_selftest_wait_timeout(tables: Tables, limit_cycles: int, stream=None) ->
     _check(lib().pip_selftest_wait_timeout(tables, scratch.data_ptr(), int(limit_cycles), _stream(stream)),
            "pip_selftest_wait_timeout")
     tables._keep = scratch  # the copy reads it until the kernel ends
+
+
+def pip_set_tuning_cache(path: str | None) -> None:
+    """The autotuners' JSON cache file (None turns it off)."""
+    _check(lib().pip_set_tuning_cache(os.fsencode(path) if path else None), "pip_set_tuning_cache")
 
 
 def pip_fma_peak(sink: torch.Tensor, blocks_per_sm: int = 8, iters: int = 4096, stream=None) -> int:

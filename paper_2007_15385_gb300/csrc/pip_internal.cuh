@@ -12,6 +12,8 @@
 //   counters        refine count, work counter, worst status
 #pragma once
 
+#include <string>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -165,6 +167,10 @@ cudaError_t launch_stream_pipelined(const pip_tables *t, const void *pts, bool i
 cudaError_t launch_stream_pipelined_i32(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, bool early,
                                         cudaStream_t s);
 cudaError_t stream_kernels_setup_i32();
+// pip_tuning.cu: the autotuners' JSON cache (no-ops while no cache file is set)
+std::string tuning_key(const pip_tables *t, const char *kernel, int64_t num_points, int pdtype);
+bool tuning_lookup(const std::string &key, int *variant, float *ms);
+void tuning_store(const std::string &key, int variant, float ms);
 // pip_stream.cu: the comparators (op 1 = sign of offset, 2 = ray crossing) on
 // one float polygon through the pipelined single-polygon kernel
 cudaError_t launch_cmp_stream(const pip_tables *t, const float *pts, int64_t M, uint32_t *mask, int op,

@@ -130,6 +130,16 @@ extern "C" pip_status pip_autotune_stream(pip_tables *t, const void *d_points, p
     pip_status st = check_tables(t);
     if (st != PIP_OK) return st;
     if (t->P != 1 || num_points <= 0 || reps < 1 || !aligned(d_points, 16)) return PIP_E_INVALID_ARG;
+    // a cached choice for this kernel, GPU and shape skips the timing runs
+    const std::string key = tuning_key(t, "stream", num_points, pdtype);
+    int cached = -1;
+    float cached_ms = 0.f;
+    if (tuning_lookup(key, &cached, &cached_ms) && cached >= 0 && cached < kNumStreamVariants) {
+        t->stream_variant = cached;
+        if (best_variant) *best_variant = cached;
+        if (best_ms) *best_ms = cached_ms;
+        return PIP_OK;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     PIP_CUDA_TRY(cudaEventCreate(&e0));
@@ -163,6 +173,7 @@ extern "C" pip_status pip_autotune_stream(pip_tables *t, const void *d_points, p
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out != PIP_OK) return out;
+    tuning_store(key, best, best_t);
     t->stream_variant = best;
     if (best_variant) *best_variant = best;
     if (best_ms) *best_ms = best_t;

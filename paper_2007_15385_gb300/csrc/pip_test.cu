@@ -613,6 +613,16 @@ extern "C" pip_status pip_autotune_batch(pip_tables *t, const void *d_points, pi
     if (st != PIP_OK) return st;
     if (num_points <= 0 || reps < 1 || d_point_offsets == nullptr || !aligned(d_points, 16))
         return PIP_E_INVALID_ARG;
+    // a cached choice for this kernel, GPU and shape skips the timing runs
+    const std::string key = tuning_key(t, "batch", num_points, pdtype);
+    int cached = -1;
+    float cached_ms = 0.f;
+    if (tuning_lookup(key, &cached, &cached_ms) && cached >= 0 && cached < kNumBatchVariants) {
+        t->batch_variant = cached;
+        if (best_variant) *best_variant = cached;
+        if (best_ms) *best_ms = cached_ms;
+        return PIP_OK;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     PIP_CUDA_TRY(cudaEventCreate(&e0));
@@ -646,6 +656,7 @@ extern "C" pip_status pip_autotune_batch(pip_tables *t, const void *d_points, pi
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out != PIP_OK) return out;
+    tuning_store(key, best, best_t);
     t->batch_variant = best;
     if (best_variant) *best_variant = best;
     if (best_ms) *best_ms = best_t;

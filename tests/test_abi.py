@@ -97,6 +97,8 @@ def test_host_argument_checks_of_the_other_entry_points(lib):
     assert lib.pip_penalty_forward(None, 12, None, 4, None, 10, 0.05, None, None, 0, None) == B.PIP_E_INVALID_ARG
     assert lib.pip_penalty_backward(None, 12, None, 4, None, 10, 0.05, None, None, None, None, 0,
                                     None) == B.PIP_E_INVALID_ARG
+    # the tuning cache can be set and cleared without a GPU
+    assert lib.pip_set_tuning_cache(None) == B.PIP_OK
     # the host-buffer call and the FMA calibration kernel refuse bad handles and sizes
     assert lib.pip_test_host(None, None, 0, 10, None, None, None, 8, None) == B.PIP_E_INVALID_ARG
     fm = ctypes.c_int64(0)

@@ -845,6 +845,45 @@ def test_inner_generator_outside_the_polygon_is_degenerate():
         t.close()
 
 
+def test_tuning_cache_round_trip(tmp_path):
+    """pip_set_tuning_cache: the first autotune times the variants and records
+    the winner under (kernel, GPU name, shape); the next one on the same shape
+    takes the recorded entry, even one edited by hand, without timing."""
+    import json
+    path = str(tmp_path / "tuning.json")
+    B.pip_set_tuning_cache(path)
+    try:
+        w = wl.gis_batch(seed=57, num_polygons=30, m_range=(1000, 20000))
+        v, vo = torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev())
+        p, po = torch.from_numpy(w.points).to(dev()), torch.from_numpy(w.point_offsets).to(dev())
+        t = B.pip_prepare(v, vo, max_points=w.num_points)
+        mask = torch.empty((w.num_points + 31) // 32, dtype=torch.int32, device=dev())
+        best, ms = B.pip_autotune_batch(t, p, po, mask, reps=2)
+        entries = json.load(open(path))
+        (key, rec), = entries.items()
+        assert key.startswith("batch|") and "polygons=30" in key and "points=%d" % w.num_points in key
+        assert rec["variant"] == best
+        other = (best + 1) % B.lib().pip_batch_variant_count()
+        entries[key] = {"variant": other, "ms": 1.5}
+        json.dump(entries, open(path, "w"))
+        again, ms2 = B.pip_autotune_batch(t, p, po, mask, reps=2)
+        assert again == other and ms2 == pytest.approx(1.5)
+        got, _ = B.pip_test(t, p, po, mask=mask)
+        assert_same(B.unpack_mask(got, w.num_points).cpu().numpy(), oracle_own(w), "cached tile shape")
+        t.close()
+        one = wl.vehicle_footprint(seed=58, m=1 << 20)
+        t1 = B.pip_prepare(torch.from_numpy(one.vertices).to(dev()), torch.from_numpy(one.vertex_offsets).to(dev()),
+                           max_points=one.num_points)
+        p1 = torch.from_numpy(one.points).to(dev())
+        m1 = torch.empty((one.num_points + 31) // 32, dtype=torch.int32, device=dev())
+        sbest, _ = B.pip_autotune_stream(t1, p1, m1, reps=2)
+        assert len(json.load(open(path))) == 2
+        assert B.pip_autotune_stream(t1, p1, m1, reps=2)[0] == sbest
+        t1.close()
+    finally:
+        B.pip_set_tuning_cache(None)
+
+
 def test_repeated_calls_reset_the_refine_queue():
     w = wl.integer_hulls(seed=22, num_polygons=8, points_per_polygon=1000)
     v = torch.from_numpy(w.vertices).to(dev())
