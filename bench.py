@@ -862,11 +862,12 @@ def bench_workload(name: str, B, wl, dev, stream, steps: int, warmup: int, fma_p
             cms = time_steps(cull, steps, 3, stream)
             out["culled"] = {"ms_per_step": cms, "effective_Gtests_per_s": tests / (cms * 1e-3) / 1e9,
                              "note": "PIP_CULL: polygons skipped per warp by bounding box, early stop"}
-        # our kernels per call: batch = items prefix, item fill, bulk, refine;
+        # our kernels per call: batch = the persistent kernel and the refine
+        # (integer polygons with integer points: the persistent kernel alone);
         # all pairs = bulk, finalize, refine; one polygon = the pipelined
         # kernel (refine inline), or bulk + refine for unaligned points
         if po is not None:
-            out["gpu_launches_per_step"] = 4
+            out["gpu_launches_per_step"] = 1 if w.points.dtype == np.int32 and w.vertices.dtype == np.int32 else 2
         elif w.num_polygons > 1:
             out["gpu_launches_per_step"] = 3
         else:

@@ -105,14 +105,14 @@ struct pip_tables {
     pip::PolyInfo *d_poly;
     uint32_t *d_queue;
     uint32_t *d_keys;            // [max_points] all-pairs candidate keys
-    int64_t *d_items;            // [P+1] work-item prefix of the own-polygon schedule
-    void *d_ritems;              // [ritems_cap] work items of the pipelined own-polygon kernel
-    int64_t ritems_cap;
+    int64_t *d_items;            // [P+1] work-item prefix of the register-streaming own-polygon schedule
     unsigned int *d_qcount;      // refine queue length of the last pip_test
     unsigned int *d_work;        // next work item of the persistent kernel
     int32_t *d_worst;            // worst polygon status
     int32_t *d_error;            // runtime error of a kernel (PIP_E_TIMEOUT), sticky until read
     void *d_stream_ctr;          // counters of the pipelined kernel (zero between launches)
+    unsigned int *d_batch_ctr;   // the pipelined batch kernel: next chunk, queue fill, ticket (zero
+                                 // between launches)
     int stream_variant;          // tile shape of the pipelined single-polygon kernel
     int batch_variant;           // tile shape of the pipelined own-polygon batch kernel
     // one-polygon tables: a host copy of the polygon's row and coefficients,

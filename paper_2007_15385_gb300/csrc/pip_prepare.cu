@@ -178,10 +178,6 @@ static pip_status prepare_impl(const void *d_vertices, pip_dtype vdtype, const i
     const size_t o_cg64 = take(vdtype == PIP_F32 ? P * kPadStride * sizeof(double2) : 0);
     const size_t o_poly = take(P * sizeof(PolyInfo));
     const size_t o_items = take((P + 1) * sizeof(int64_t));
-    // items of the pipelined own-polygon kernel: a range [a, b) touches at most
-    // (b - a) / tile + 2 chunks of the grid (tile >= 2048 points, 16 B an item)
-    t->ritems_cap = (max_points > 0 ? max_points : 0) / 2048 + 2 * (int64_t)P + 2;
-    const size_t o_ritems = take((size_t)t->ritems_cap * 16);
     const size_t o_cnt = take(128);
     // refine queue: every point once, plus the slack of the pipelined kernel's
     // per-CTA slices (at most one tile of 4,096 points per CTA, 2 CTAs per SM)
@@ -210,12 +206,12 @@ static pip_status prepare_impl(const void *d_vertices, pip_dtype vdtype, const i
     t->d_cmp_g64 = vdtype == PIP_F32 ? (double2 *)(b + o_cg64) : nullptr;
     t->d_poly = (PolyInfo *)(b + o_poly);
     t->d_items = (int64_t *)(b + o_items);
-    t->d_ritems = (void *)(b + o_ritems);
     t->d_qcount = (unsigned int *)(b + o_cnt);
     t->d_work = (unsigned int *)(b + o_cnt + 16);
     t->d_worst = (int32_t *)(b + o_cnt + 32);
     t->d_error = (int32_t *)(b + o_cnt + 48);
     t->d_stream_ctr = (void *)(b + o_cnt + 64);
+    t->d_batch_ctr = (unsigned int *)(b + o_cnt + 96);
     t->d_queue = (uint32_t *)(b + o_queue);
     t->d_keys = (uint32_t *)(b + o_keys);
 

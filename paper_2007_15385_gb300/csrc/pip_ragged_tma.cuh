@@ -2,25 +2,34 @@
 // with its own contiguous range of points (Alg. 5 per point against its own
 // polygon only).
 //
-// Schedule.  The point array is cut at a fixed grid of kTile-point chunks;
-// a work item is one polygon's points inside one chunk, {j, k, lo, hi}, the
-// points k*kTile + [lo, hi).  A single-block kernel validates the point
-// offsets and forms the prefix of the items per polygon; a many-block kernel
-// (one warp per polygon) writes the item table (items of one polygon are
-// consecutive) and zeroes the mask words that straddle two polygons' ranges.
+// Schedule.  The point array is cut at a fixed grid of kTile-point chunks, and
+// one persistent launch works through the chunks: a CTA's producer warp takes
+// the next chunk from a global counter (dynamic balance: polygons have 3 to
+// 64 edges and 10^3 to 10^5 points), finds the chunk's first polygon by a
+// 32-way search over the device point offsets (three dependent loads for
+// 4,096 polygons), reads the next 32 offsets in one load, and packs the
+// chunk's polygons, up to K of them, into a stage of the shared-memory ring:
+// one bulk copy of their points (contiguous: the polygons' ranges are
+// consecutive), their padded coefficient rows and their PolyInfo rows.  A
+// chunk with more than K polygons takes several stages.  Before the loop
+// every CTA checks a share of the offsets (non-decreasing, 0 .. M); the last
+// CTA to finish resets the counters, so that one launch is the whole bulk
+// test and no setup kernel is needed.
 //
 // Persistent CTAs, one producer warp and seven consumer warps (16 warps per SM
-// at two CTAs: 128 registers a thread, 16 points per lane).  The producer
-// takes the next item from a global counter (dynamic balance: polygons have
-// 3 to 64 edges and 10^3 to 10^5 points) and bulk-copies into a ring stage:
-// the item's points, the polygon's padded coefficient row and its PolyInfo
-// row; a small header names the item.  Consumers split the item into
-// 32*PPL-point slices on the chunk grid (rotating over warps from item to
-// item) and evaluate s_k = t_k - x w_kx - y w_ky with the first three edges
-// peeled, four edges per step and an exact 0-3 edge tail.  Mask words inside
-// a polygon's range are stored, words shared with a neighbour are OR-ed into
-// the zeroed word.  Uncertain points go to the global refine queue, decided
-// by the refine launch that follows.
+// at two CTAs: 128 registers a thread, 16 points per lane).  Consumers split
+// the stage's points into 32*PPL-point slices on the chunk grid (one slice per
+// warp, rotating over warps from stage to stage) and evaluate, for each of the
+// stage's polygons that a slice meets, s_k = t_k - x w_kx - y w_ky with the
+// first three edges peeled, four edges per step and an exact 0-3 edge tail.
+// Mask words inside a polygon's range are stored; a word shared with a
+// neighbouring polygon is written by each polygon through an AND that clears
+// its own bits and an OR of its results, so the neighbours' writes commute.
+// Uncertain points go to the global refine queue, decided by the refine
+// launch that follows.  Integer polygons with integer points (EXACT) are
+// decided exactly in the consumers instead, from the polygon's staged integer
+// edge row (float32 determinants with an exact sign, or int64 beyond
+// +-2^22), so that nothing is queued and no refine launch follows.
 #pragma once
 
 #include "pip_kernels.cuh"
@@ -30,29 +39,29 @@ namespace {
 
 using namespace pip;
 
-struct RaggedItem {
-    int32_t j, k, lo, hi;
-};
-
-struct RaggedHeader {
-    int32_t j, k, lo, hi;
-    int32_t rot, pad0, pad1, pad2;
-};
-
 constexpr int kRaggedWarps = 7;  // consumer warps
 constexpr int kRaggedThreads = (kRaggedWarps + 1) * 32;
+constexpr int kMaxPack = 4;      // polygons per stage, at most
 
-// ROWS: 16-byte entries per edge of the staged polygon row (2 for the ray
-// comparator, 1 otherwise).
-template <int PPL, int STAGES, int ROWS = 1>
+// The stage's header: its chunk, its polygons (indices and point ranges
+// relative to the chunk, in order) and the consumers' rotation; np < 0 ends
+// the CTA's loop.
+struct RaggedHeader {
+    int32_t c, np, rot, pad;
+    int32_t j[kMaxPack], lo[kMaxPack], hi[kMaxPack];
+};
+
+// K: polygons per stage (1, 2 or 4).  ROWS: 16-byte entries per edge of a
+// staged polygon row (2 for the ray comparator, 1 otherwise).
+template <int PPL, int STAGES, int K = 1, int ROWS = 1>
 struct RaggedCfg {
     static constexpr int kSlice = 32 * PPL;
-    static constexpr int kTile = kRaggedWarps * kSlice;  // points per item, at most
+    static constexpr int kTile = kRaggedWarps * kSlice;  // points per chunk
     static constexpr size_t kPtsBytes = (size_t)kTile * 8;
     static constexpr size_t kCoefOff = kPtsBytes;
     static constexpr size_t kRowBytes = (size_t)ROWS * kPadStride * sizeof(float4);
-    static constexpr size_t kInfoOff = kCoefOff + kRowBytes;
-    static constexpr size_t kHdrOff = kInfoOff + sizeof(PolyInfo);
+    static constexpr size_t kInfoOff = kCoefOff + K * kRowBytes;
+    static constexpr size_t kHdrOff = kInfoOff + K * sizeof(PolyInfo);
     static constexpr size_t kStageBytes = (kHdrOff + sizeof(RaggedHeader) + 127) & ~(size_t)127;
     static constexpr size_t kBarOff = STAGES * kStageBytes;
     static constexpr size_t kSmem = kBarOff + 2 * STAGES * sizeof(uint64_t);
@@ -60,100 +69,47 @@ struct RaggedCfg {
     static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
 };
 
-// Single block: the offsets' check and the exclusive prefix of the items per
-// polygon.  Items of polygon j are the chunks of the kTile grid its range
-// [poffs[j], poffs[j+1]) touches.  Bad offsets (not a non-decreasing cover of
-// [0, M)), or more items than the table holds, leave a total prefix[P] of zero
-// and raise PIP_E_INVALID_ARG in *worst.
-__global__ void __launch_bounds__(1024) ragged_items_kernel(
-    const int64_t *__restrict__ poffs, int P, int64_t M, int tile, int64_t *__restrict__ prefix, int64_t cap,
-    unsigned int *__restrict__ counters, unsigned int *__restrict__ qcount, int32_t *__restrict__ worst)
+// The batch kernel's counters, zero between launches: the next chunk, the
+// refine queue's fill, the CTAs that have finished.
+struct BatchCounters {
+    unsigned int chunk, qfill, ticket;
+};
+
+// Largest j in [0, P) with poffs[j] <= x (the polygon holding point x when the
+// offsets are a non-decreasing cover), by the whole warp, 32 probes a round.
+__device__ __forceinline__ int find_polygon(const int64_t *__restrict__ poffs, int P, int64_t x, int lane)
 {
-    __shared__ int64_t warp_tot[32];
-    __shared__ int64_t carry;
-    __shared__ int bad;
-    if (threadIdx.x == 0) {
-        carry = 0;
-        bad = 0;
-        counters[0] = 0;  // next item
-        *qcount = 0;
+    int lo = 0, hi = P;  // poffs[lo] <= x holds for lo = 0 (offsets start at 0)
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) / 32;
+        const int probe = lo + lane * step;
+        const bool le = probe < hi && poffs[probe] <= x;
+        const unsigned b = __ballot_sync(0xffffffffu, le) | 1u;
+        const int L = 31 - __clz((int)b);
+        lo = lo + L * step;
+        hi = min(hi, lo + step);
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int base = 0; base < P; base += blockDim.x) {
-        const int j = base + threadIdx.x;
-        int64_t cnt = 0;
-        if (j < P) {
-            const int64_t a = poffs[j], b = poffs[j + 1];
-            if (a < 0 || b < a || b > M || (j == 0 && a != 0) || (j == P - 1 && b != M)) bad = 1;
-            else if (b > a) cnt = (b - 1) / tile - a / tile + 1;
-        }
-        int64_t v = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        if (lane == 31) warp_tot[wid] = v;
-        __syncthreads();
-        if (wid == 0) {
-            int64_t w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t u = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += u;
-            }
-            warp_tot[lane] = w;
-        }
-        __syncthreads();
-        const int64_t excl = carry + (wid ? warp_tot[wid - 1] : 0) + v - cnt;
-        if (j < P) prefix[j] = excl;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = excl + cnt;
-        __syncthreads();
-    }
-    const bool ok = !bad && carry <= cap;
-    if (threadIdx.x == 0) {
-        prefix[P] = ok ? carry : 0;
-        if (!ok) atomicMax(worst, (int)PIP_E_INVALID_ARG);
-    }
+    return lo;
 }
 
-// One warp per polygon, many blocks: the polygon's items (lane-strided), and
-// zeros in the mask words it shares with its neighbours (they are OR-ed into
-// later).  Nothing when the prefix pass found the offsets bad (total zero).
-__global__ void __launch_bounds__(256) ragged_fill_kernel(const int64_t *__restrict__ poffs, int P, int tile,
-                                                          const int64_t *__restrict__ prefix,
-                                                          RaggedItem *__restrict__ items,
-                                                          uint32_t *__restrict__ mask)
+// The slice's PPL mask words.  Words wholly inside the polygon's range are
+// stored (16-byte stores when aligned); a word shared with a neighbour gets an
+// AND that clears the polygon's own bits and an OR of its results, so that
+// the neighbours' writes commute and no word needs zeroing first.  A polygon
+// owns its points' bits [a, b) and, when it holds the last point (bw > b),
+// the bits past it up to bw (the end of the last word), which become 0.
+__device__ __forceinline__ uint32_t own_bits(int64_t w0, int64_t a, int64_t bw)
 {
-    const int64_t total = prefix[P];
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < P; j += nwarps) {
-        const int64_t a = poffs[j], b = poffs[j + 1];
-        if (b <= a) continue;
-        const int64_t k0 = a / tile, nk = (b - 1) / tile - k0 + 1;
-        const int64_t i0 = prefix[j];
-        if (i0 < 0 || i0 + nk > total) continue;
-        if (lane == 0 && (a & 31)) mask[a >> 5] = 0u;
-        if (lane == 1 && (b & 31)) mask[(b - 1) >> 5] = 0u;
-        for (int64_t r = lane; r < nk; r += 32) {
-            const int64_t c0 = (k0 + r) * tile;
-            RaggedItem it;
-            it.j = j;
-            it.k = (int32_t)(k0 + r);
-            it.lo = (int32_t)(max(a, c0) - c0);
-            it.hi = (int32_t)(min(b, c0 + tile) - c0);
-            items[i0 + r] = it;
-        }
-    }
+    const int64_t lo = max(a, w0) - w0, hi = min(bw, w0 + 32) - w0;
+    if (hi <= lo) return 0u;
+    const uint32_t upto = hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    return upto & ~((1u << lo) - 1u);
 }
 
-// The slice's PPL mask words: words wholly inside the polygon's range are
-// stored (16-byte stores when aligned), words shared with a neighbour are
-// OR-ed into the word the fill kernel zeroed.
 template <int PPL, bool TAIL>
 __device__ __forceinline__ void ragged_store_words(const uint32_t (&w_in)[PPL], int64_t gs, int64_t a, int64_t b,
-                                                   int lane, uint32_t *__restrict__ mask, bool vec_store)
+                                                   int64_t bw, int lane, uint32_t *__restrict__ mask,
+                                                   bool vec_store)
 {
     uint32_t *mw = mask + (gs >> 5);
     if (!TAIL) {
@@ -177,8 +133,15 @@ __device__ __forceinline__ void ragged_store_words(const uint32_t (&w_in)[PPL], 
             if (lane == q) myword = w_in[q];
         if (lane < PPL) {
             const int64_t w0 = gs + 32 * lane;  // first point of this lane's word
-            if (w0 >= a && w0 + 32 <= b) mw[lane] = myword;        // wholly this polygon's
-            else if (w0 < b && w0 + 32 > a && myword) atomicOr(&mw[lane], myword);  // shared, zeroed
+            if (w0 >= a && w0 + 32 <= bw) {
+                mw[lane] = myword;  // wholly this polygon's
+            } else {
+                const uint32_t own = own_bits(w0, a, bw);
+                if (own) {
+                    atomicAnd(&mw[lane], ~own);
+                    if (myword & own) atomicOr(&mw[lane], myword & own);
+                }
+            }
         }
     }
 }
@@ -193,7 +156,7 @@ __device__ __forceinline__ void ragged_store_words(const uint32_t (&w_in)[PPL], 
 template <int PPL, bool INT, bool CENTER, bool TAIL, bool EARLY = false>
 __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, float oy, float b0, float b1,
                                              const unsigned char *rows, const void *__restrict__ pts,
-                                             int64_t gs, int64_t a, int64_t b, int lane,
+                                             int64_t gs, int64_t a, int64_t b, int64_t bw, int lane,
                                              uint32_t *__restrict__ mask, bool vec_store, int j,
                                              uint32_t *__restrict__ queue, uint32_t *__restrict__ qpoly,
                                              unsigned int *__restrict__ qcount)
@@ -332,7 +295,7 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
             base += (unsigned int)__popc(u[q]);
         }
     }
-    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, lane, mask, vec_store);
+    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, bw, lane, mask, vec_store);
 }
 
 // Integer polygon and integer points, decided exactly here: no filter, no
@@ -354,7 +317,7 @@ template <int PPL, bool TAIL>
 __device__ __forceinline__ void ragged_slice_exact(const float4 *fs, const int4 *__restrict__ irow, int n,
                                                    bool poly_small, const unsigned char *rows,
                                                    const void *__restrict__ pts, int64_t gs, int64_t a, int64_t b,
-                                                   int lane, uint32_t *__restrict__ mask, bool vec_store)
+                                                   int64_t bw, int lane, uint32_t *__restrict__ mask, bool vec_store)
 {
     constexpr int kLim = 1 << 22;
     int px[PPL], py[PPL];
@@ -423,7 +386,7 @@ __device__ __forceinline__ void ragged_slice_exact(const float4 *fs, const int4 
 #pragma unroll
         for (int q = 0; q < PPL; ++q) w_in[q] = __ballot_sync(0xffffffffu, valid[q] && neg[q] >= 0);
     }
-    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, lane, mask, vec_store);
+    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, bw, lane, mask, vec_store);
 }
 
 // What a batch slice decides: the Voronoi test (filter, or exact for integer
@@ -440,7 +403,7 @@ constexpr int kRagVoronoi = 0, kRagSign = 1, kRagRay = 2, kRagFp64 = 3;
 template <int OP, int PPL, bool TAIL>
 __device__ __forceinline__ void ragged_slice_cmp(const float4 *cs, int n, const unsigned char *rows,
                                                  const void *__restrict__ pts, int64_t gs, int64_t a, int64_t b,
-                                                 int lane, uint32_t *__restrict__ mask, bool vec_store)
+                                                 int64_t bw, int lane, uint32_t *__restrict__ mask, bool vec_store)
 {
     float xs[PPL], ys[PPL];
     bool valid[PPL];
@@ -519,17 +482,23 @@ __device__ __forceinline__ void ragged_slice_cmp(const float4 *cs, int n, const 
     uint32_t w_in[PPL];
 #pragma unroll
     for (int q = 0; q < PPL; ++q) w_in[q] = __ballot_sync(0xffffffffu, valid[q] && in[q]);
-    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, lane, mask, vec_store);
+    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, bw, lane, mask, vec_store);
 }
 
-// A polygon that failed validation contains no point: its words are zero.
+// A polygon that failed validation contains no point: its whole words are
+// zero, its bits of shared words are cleared.
 template <int PPL>
-__device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_t b, int lane,
+__device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_t bw, int lane,
                                                    uint32_t *__restrict__ mask)
 {
     if (lane < PPL) {
         const int64_t w0 = gs + 32 * lane;
-        if (w0 >= a && w0 + 32 <= b) mask[(gs >> 5) + lane] = 0u;
+        if (w0 >= a && w0 + 32 <= bw) {
+            mask[(gs >> 5) + lane] = 0u;
+        } else {
+            const uint32_t own = own_bits(w0, a, bw);
+            if (own) atomicAnd(&mask[(gs >> 5) + lane], ~own);
+        }
     }
 }
 
@@ -537,17 +506,18 @@ __device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_
 // float32 edge rows (a_x, a_y, e_x, e_y) and every point is decided exactly in
 // the consumers (nothing is queued); `ipad` holds the int64 rows for points or
 // polygons beyond +-2^22.  OP other than kRagVoronoi: a comparator, `coefp`
-// its row table (float polygons and points), nothing queued.
-template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false>
+// its row table (float polygons and points), nothing queued.  K: polygons per
+// stage.  `qcount` receives the number of queued points (the refine's count).
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false, int K = 1>
 __global__ void __launch_bounds__(kRaggedThreads,
-                                  RaggedCfg<PPL, STAGES, OP == kRagRay ? 2 : 1>::kMinBlocks) ragged_tma_kernel(
+                                  RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1>::kMinBlocks) ragged_tma_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, const int4 *__restrict__ ipad,
-    const void *__restrict__ pts,
-    const RaggedItem *__restrict__ items, const int64_t *__restrict__ prefix, int P,
-    unsigned int *__restrict__ counters, uint32_t *__restrict__ mask, uint32_t *__restrict__ queue,
-    uint32_t *__restrict__ qpoly, unsigned int *__restrict__ qcount, int *__restrict__ err)
+    const void *__restrict__ pts, int64_t M, const int64_t *__restrict__ poffs, int P,
+    BatchCounters *__restrict__ ctr, uint32_t *__restrict__ mask, uint32_t *__restrict__ queue,
+    uint32_t *__restrict__ qpoly, unsigned int *__restrict__ qcount, int32_t *__restrict__ worst,
+    int *__restrict__ err)
 {
-    using C = RaggedCfg<PPL, STAGES, OP == kRagRay ? 2 : 1>;
+    using C = RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1>;
     constexpr int kSlice = C::kSlice;
     constexpr int kTile = C::kTile;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -561,66 +531,156 @@ __global__ void __launch_bounds__(kRaggedThreads,
         }
         fence_mbar_init();
     }
+    // this CTA's share of the offsets' check: a non-decreasing cover of [0, M)
+    for (int j = blockIdx.x * blockDim.x + tid; j < P; j += gridDim.x * blockDim.x) {
+        const int64_t a = poffs[j], b = poffs[j + 1];
+        if (a < 0 || b < a || b > M || (j == 0 && a != 0) || (j == P - 1 && b != M))
+            atomicMax(worst, (int)PIP_E_INVALID_ARG);
+    }
     __syncthreads();
+    const int64_t nchunks = (M + kTile - 1) / kTile;
+    const int64_t last_word_end = (M + 31) & ~(int64_t)31;
 
     if (warp == kRaggedWarps) {
-        // ---------------- producer: one lane takes items and issues the copies
-        if (lane == 0) {
-            // items are taken two ahead of the one being issued, so that the
-            // counter's round trip and the item row's load overlap the waits
-            const int64_t total = prefix[P];
-            auto grab = [&](int64_t prev) -> int64_t {
-                return prev < total ? (int64_t)atomicAdd(&counters[0], 1u) : total;
-            };
-            int64_t cur = grab(0);
-            int64_t nxt = grab(cur);
-            RaggedItem ci{};
-            if (cur < total) ci = items[cur];
-            int it = 0, s = 0;
-            uint32_t ephase = 0;
-            int rot = 0;
-            bool fail = false;
-            for (;; ++it) {
-                const int64_t after = grab(nxt);
-                RaggedItem ni{};
-                if (nxt < total) ni = items[nxt];
-                if (it >= STAGES && !mbar_wait(&empty[s], ephase, err)) {
-                    fail = true;
-                    break;
+        // ---------------- producer: the whole warp finds a chunk's polygons,
+        // lane 0 fills the stages
+        int it = 0, s = 0;
+        uint32_t ephase = 0;
+        int rot = 0;
+        bool fail = false;
+        // chunks come in runs of consecutive chunks (guided: up to 8, fewer as the
+        // work runs out), so that within a run the polygon walk continues from
+        // the previous chunk instead of searching the offsets again
+        unsigned int run_c = 0, run_end = 0;
+        int jnext = 0;
+        // the next chunk's offset window, loaded before this chunk's stages are
+        // issued so that its latency hides behind the waits for free stages
+        constexpr int64_t kBeyond = (int64_t)1 << 62;
+        int pre_j = -1;
+        int64_t pre_a = 0, pre_b = 0;
+        for (;;) {
+            if (run_c >= run_end) {
+                unsigned int c = 0, len = 1;
+                if (lane == 0) {
+                    const unsigned int seen = *(volatile unsigned int *)&ctr->chunk;
+                    const int64_t left = nchunks - (int64_t)seen;
+                    len = (unsigned int)max((int64_t)1, min((int64_t)8, left / (16 * (int64_t)gridDim.x)));
+                    c = atomicAdd(&ctr->chunk, len);
                 }
-                unsigned char *st = smem + (size_t)s * C::kStageBytes;
-                RaggedHeader *h = (RaggedHeader *)(st + C::kHdrOff);
-                if (cur >= total) {
-                    h->j = -1;
-                    mbar_arrive(&full[s]);  // release: the header is visible to the consumers
-                    break;
-                }
-                const int64_t c0 = (int64_t)ci.k * kTile;
-                const int64_t sa = (c0 + ci.lo) & ~(int64_t)1, eb = (c0 + ci.hi) & ~(int64_t)1;
-                const uint32_t pbytes = eb > sa ? (uint32_t)((eb - sa) * 8) : 0u;
-                h->j = ci.j;
-                h->k = ci.k;
-                h->lo = ci.lo;
-                h->hi = ci.hi;
-                h->rot = rot;
-                rot = (rot + (ci.hi - 1) / kSlice - ci.lo / kSlice + 1) % kRaggedWarps;
-                const uint32_t cbytes = (uint32_t)C::kRowBytes;
-                mbar_arrive_expect_tx(&full[s], pbytes + cbytes + (uint32_t)sizeof(PolyInfo));
-                if (pbytes) bulk_copy_g2s(st + (sa - c0) * 8, (const char *)pts + sa * 8, pbytes, &full[s]);
-                bulk_copy_g2s(st + C::kCoefOff, (const char *)coefp + (size_t)ci.j * C::kRowBytes, cbytes, &full[s]);
-                bulk_copy_g2s(st + C::kInfoOff, poly + ci.j, (uint32_t)sizeof(PolyInfo), &full[s]);
-                cur = nxt;
-                nxt = after;
-                ci = ni;
-                if (++s == STAGES) {
-                    s = 0;
-                    if (it + 1 >= 2 * STAGES) ephase ^= 1u;
-                }
+                c = __shfl_sync(0xffffffffu, c, 0);
+                len = __shfl_sync(0xffffffffu, len, 0);
+                if ((int64_t)c >= nchunks) break;
+                run_c = c;
+                run_end = (unsigned int)min((int64_t)c + len, nchunks);
+                jnext = find_polygon(poffs, P, (int64_t)c * kTile, lane);
             }
+            const unsigned int c = run_c++;
+            const int64_t c0 = (int64_t)c * kTile, c1 = min(c0 + kTile, M);
+            int j = jnext;
+            // the chunk's polygons, in groups of up to K non-empty ones
+            while (j < P) {
+                // lane i: polygon j + i and its range clipped to the chunk
+                const int jj = j + lane;
+                int64_t ra, rb;
+                if (j == pre_j) {  // warp-uniform
+                    ra = pre_a;
+                    rb = pre_b;
+                } else {
+                    ra = jj < P ? poffs[jj] : kBeyond;
+                    rb = jj < P ? poffs[jj + 1] : kBeyond;
+                }
+                pre_j = -1;
+                const int64_t pa = jj < P ? max(ra, c0) : c1, pb = jj < P ? min(rb, c1) : c1;
+                const bool starts = jj < P && ra < c1;  // meets the chunk or lies beyond it
+                const bool meets = starts && pb > pa;
+                const unsigned mm = __ballot_sync(0xffffffffu, meets);
+                const unsigned beyond = __ballot_sync(0xffffffffu, !starts);
+                // polygons before the first lane that lies beyond the chunk belong to it
+                const int nlanes = beyond ? __ffs(beyond) - 1 : 32;
+                unsigned todo = mm & (nlanes == 32 ? 0xffffffffu : ((1u << nlanes) - 1u));
+                if (nlanes < 32 && run_c < run_end) {
+                    // the next chunk of this run starts with the last polygon
+                    // that starts before c1: load its window now
+                    pre_j = j + max(nlanes - 1, 0);
+                    const int jq = pre_j + lane;
+                    pre_a = jq < P ? poffs[jq] : kBeyond;
+                    pre_b = jq < P ? poffs[jq + 1] : kBeyond;
+                }
+                while (todo) {
+                    // the next group: up to K polygons of `todo`, in order
+                    int gj[K], glo[K], ghi[K];
+                    int np = 0;
+#pragma unroll
+                    for (int q = 0; q < K; ++q) {
+                        gj[q] = 0;
+                        glo[q] = ghi[q] = 0;
+                        if (todo) {  // warp-uniform
+                            const int l = __ffs(todo) - 1;
+                            todo &= todo - 1;
+                            gj[q] = j + l;
+                            glo[q] = (int)(__shfl_sync(0xffffffffu, pa, l) - c0);
+                            ghi[q] = (int)(__shfl_sync(0xffffffffu, pb, l) - c0);
+                            np = q + 1;
+                        }
+                    }
+                    if (lane == 0) {
+                        if (it >= STAGES && !mbar_wait(&empty[s], ephase, err)) fail = true;
+                        if (!fail) {
+                            unsigned char *st = smem + (size_t)s * C::kStageBytes;
+                            RaggedHeader *h = (RaggedHeader *)(st + C::kHdrOff);
+                            h->c = (int32_t)c;
+                            h->np = np;
+                            h->rot = rot;
+#pragma unroll
+                            for (int q = 0; q < K; ++q) {
+                                h->j[q] = gj[q];
+                                h->lo[q] = glo[q];
+                                h->hi[q] = ghi[q];
+                            }
+                            const int lo = glo[0], hi = ghi[np - 1];
+                            rot = (rot + (hi - 1) / kSlice - lo / kSlice + 1) % kRaggedWarps;
+                            const int64_t sa = (c0 + lo) & ~(int64_t)1, eb = (c0 + hi) & ~(int64_t)1;
+                            const uint32_t pbytes = eb > sa ? (uint32_t)((eb - sa) * 8) : 0u;
+                            const uint32_t rbytes = (uint32_t)C::kRowBytes;
+                            mbar_arrive_expect_tx(&full[s], pbytes + (uint32_t)np * (rbytes + (uint32_t)sizeof(PolyInfo)));
+                            if (pbytes)
+                                bulk_copy_g2s(st + (sa - c0) * 8, (const char *)pts + sa * 8, pbytes, &full[s]);
+                            for (int q = 0; q < np; ++q) {
+                                bulk_copy_g2s(st + C::kCoefOff + q * C::kRowBytes,
+                                              (const char *)coefp + (size_t)gj[q] * C::kRowBytes, rbytes, &full[s]);
+                                bulk_copy_g2s(st + C::kInfoOff + q * sizeof(PolyInfo), poly + gj[q],
+                                              (uint32_t)sizeof(PolyInfo), &full[s]);
+                            }
+                            if (++s == STAGES) {
+                                s = 0;
+                                if (it + 1 >= 2 * STAGES) ephase ^= 1u;
+                            }
+                            ++it;
+                        }
+                    }
+                    fail = __shfl_sync(0xffffffffu, fail, 0);
+                    if (fail) break;
+                }
+                if (fail) break;
+                if (nlanes < 32) {
+                    // the next chunk starts with the last polygon that starts before c1
+                    jnext = j + max(nlanes - 1, 0);
+                    break;
+                }
+                j += 32;  // more than 32 polygons meet this chunk: the next window
+            }
+            if (j >= P) jnext = P - 1;
+            if (fail) break;
+        }
+        if (lane == 0) {
             if (fail) {
                 // gave up: let the copies already issued land before the CTA leaves
                 for (int k = it > STAGES ? it - STAGES : 0; k < it; ++k)
                     mbar_wait(&full[k % STAGES], (uint32_t)((k / STAGES) & 1), err);
+            } else if (it < STAGES || mbar_wait(&empty[s], ephase, err)) {
+                RaggedHeader *h = (RaggedHeader *)(smem + (size_t)s * C::kStageBytes + C::kHdrOff);
+                h->np = -1;
+                mbar_arrive(&full[s]);  // release: the header is visible to the consumers
             }
         }
     } else {
@@ -631,44 +691,56 @@ __global__ void __launch_bounds__(kRaggedThreads,
         for (;;) {
             if (!mbar_wait(&full[s], fphase, err)) break;
             const unsigned char *st = smem + (size_t)s * C::kStageBytes;
-            const RaggedHeader h = *(const RaggedHeader *)(st + C::kHdrOff);
-            if (h.j < 0) break;
-            const int nsl = (h.hi - 1) / kSlice - h.lo / kSlice + 1;
+            const RaggedHeader &h = *(const RaggedHeader *)(st + C::kHdrOff);  // read in place
+            if (h.np < 0) break;
+            const int lo0 = h.lo[0], hiN = h.hi[h.np - 1];
+            const int nsl = (hiN - 1) / kSlice - lo0 / kSlice + 1;
             const int r = (warp - h.rot + kRaggedWarps) % kRaggedWarps;
             if (r < nsl) {
-                const PolyInfo &pi = *(const PolyInfo *)(st + C::kInfoOff);
-                const int64_t c0 = (int64_t)h.k * kTile;
-                const int sl = h.lo / kSlice + r;
+                const int64_t c0 = (int64_t)h.c * kTile;
+                const int sl = lo0 / kSlice + r;
                 const int64_t gs = c0 + (int64_t)sl * kSlice;
-                const int64_t a = c0 + h.lo, b = c0 + h.hi;
                 const unsigned char *rows = st + (size_t)sl * kSlice * 8;
-                const float4 *cs = (const float4 *)(st + C::kCoefOff);
-                const bool whole = gs >= a && gs + kSlice <= b;
-                if (pi.status != PIP_OK) {
-                    ragged_slice_empty<PPL>(gs, a, b, lane, mask);
-                } else if (OP != kRagVoronoi) {
-                    if (whole) ragged_slice_cmp<OP, PPL, false>(cs, pi.n, rows, pts, gs, a, b, lane, mask, vec_store);
-                    else ragged_slice_cmp<OP, PPL, true>(cs, pi.n, rows, pts, gs, a, b, lane, mask, vec_store);
-                } else if (EXACT) {
-                    const int4 *irow = ipad + (size_t)h.j * kPadStride;
-                    const bool poly_small = fmaxf(fmaxf(-pi.bbox[0], -pi.bbox[1]), fmaxf(pi.bbox[2], pi.bbox[3])) <=
-                                            (float)(1 << 22);
-                    if (whole)
-                        ragged_slice_exact<PPL, false>(cs, irow, pi.n, poly_small, rows, pts, gs, a, b, lane, mask,
-                                                       vec_store);
-                    else
-                        ragged_slice_exact<PPL, true>(cs, irow, pi.n, poly_small, rows, pts, gs, a, b, lane, mask,
-                                                      vec_store);
-                } else if (whole) {
-                    if (pi.ox == 0.f && pi.oy == 0.f)
-                        ragged_slice<PPL, INT, false, false, EARLY>(cs, pi.n, 0.f, 0.f, pi.beta0, pi.beta1, rows, pts, gs,
-                                                             a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
-                    else
-                        ragged_slice<PPL, INT, true, false, EARLY>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts,
-                                                            gs, a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
-                } else {
-                    ragged_slice<PPL, INT, true, true, EARLY>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows, pts, gs,
-                                                       a, b, lane, mask, vec_store, h.j, queue, qpoly, qcount);
+#pragma unroll 1
+                for (int q = 0; q < h.np; ++q) {
+                    const int64_t a = c0 + h.lo[q], b = c0 + h.hi[q];
+                    if (b <= gs || a >= gs + kSlice) continue;  // this polygon misses the slice
+                    const int64_t bw = b == M ? last_word_end : b;
+                    const PolyInfo &pi = *(const PolyInfo *)(st + C::kInfoOff + q * sizeof(PolyInfo));
+                    const float4 *cs = (const float4 *)(st + C::kCoefOff + q * C::kRowBytes);
+                    const bool whole = gs >= a && gs + kSlice <= b;
+                    const int j = h.j[q];
+                    if (pi.status != PIP_OK) {
+                        ragged_slice_empty<PPL>(gs, a, bw, lane, mask);
+                    } else if (OP != kRagVoronoi) {
+                        if (whole)
+                            ragged_slice_cmp<OP, PPL, false>(cs, pi.n, rows, pts, gs, a, b, bw, lane, mask, vec_store);
+                        else
+                            ragged_slice_cmp<OP, PPL, true>(cs, pi.n, rows, pts, gs, a, b, bw, lane, mask, vec_store);
+                    } else if (EXACT) {
+                        const int4 *irow = ipad + (size_t)j * kPadStride;
+                        const bool poly_small =
+                            fmaxf(fmaxf(-pi.bbox[0], -pi.bbox[1]), fmaxf(pi.bbox[2], pi.bbox[3])) <= (float)(1 << 22);
+                        if (whole)
+                            ragged_slice_exact<PPL, false>(cs, irow, pi.n, poly_small, rows, pts, gs, a, b, bw, lane,
+                                                           mask, vec_store);
+                        else
+                            ragged_slice_exact<PPL, true>(cs, irow, pi.n, poly_small, rows, pts, gs, a, b, bw, lane,
+                                                          mask, vec_store);
+                    } else if (whole) {
+                        if (pi.ox == 0.f && pi.oy == 0.f)
+                            ragged_slice<PPL, INT, false, false, EARLY>(cs, pi.n, 0.f, 0.f, pi.beta0, pi.beta1, rows,
+                                                                        pts, gs, a, b, bw, lane, mask, vec_store, j,
+                                                                        queue, qpoly, &ctr->qfill);
+                        else
+                            ragged_slice<PPL, INT, true, false, EARLY>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows,
+                                                                       pts, gs, a, b, bw, lane, mask, vec_store, j,
+                                                                       queue, qpoly, &ctr->qfill);
+                    } else {
+                        ragged_slice<PPL, INT, true, true, EARLY>(cs, pi.n, pi.ox, pi.oy, pi.beta0, pi.beta1, rows,
+                                                                  pts, gs, a, b, bw, lane, mask, vec_store, j, queue,
+                                                                  qpoly, &ctr->qfill);
+                    }
                 }
             }
             __syncwarp();
@@ -677,6 +749,18 @@ __global__ void __launch_bounds__(kRaggedThreads,
                 s = 0;
                 fphase ^= 1u;
             }
+        }
+    }
+    // the last CTA to finish hands over the queue's fill and resets the counters
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned int t = atomicAdd(&ctr->ticket, 1u);
+        if (t == gridDim.x - 1) {
+            __threadfence();
+            *qcount = atomicExch(&ctr->qfill, 0u);
+            atomicExch(&ctr->chunk, 0u);
+            atomicExch(&ctr->ticket, 0u);
         }
     }
 }

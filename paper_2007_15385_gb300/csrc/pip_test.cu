@@ -57,24 +57,20 @@ cudaError_t launch_ragged(const pip_tables *t, const void *pts, int64_t M, const
 // The pipelined own-polygon batch: setup (items, shared mask words, counters)
 // then the persistent kernel.  Variants: (points per lane, ring stages); the
 // item tile is 7 consumer warps x 32 lanes x points per lane.
+// Variants of the pipelined batch kernel: (points per lane, ring stages,
+// polygons per stage).
 struct BatchVariant {
-    int ppl, stages;
+    int ppl, stages, pack;
 };
-constexpr BatchVariant kBatchVariants[] = {{16, 3}, {16, 2}, {12, 3}, {12, 4}};
+constexpr BatchVariant kBatchVariants[] = {{16, 3, 1}, {16, 3, 2}, {16, 3, 4}, {16, 2, 2}, {12, 3, 2}, {12, 4, 2}};
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false>
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false, int K = 1>
 cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
                                   uint32_t *mask, cudaStream_t s)
 {
-    using C = RaggedCfg<PPL, STAGES, OP == kRagRay ? 2 : 1>;
-    ragged_items_kernel<<<1, 1024, 0, s>>>(poffs, t->P, M, C::kTile, t->d_items, t->ritems_cap, t->d_work,
-                                           t->d_qcount, t->d_worst);
-    ragged_fill_kernel<<<(unsigned)std::min((t->P + 7) / 8, t->num_sms * 8), 256, 0, s>>>(
-        poffs, t->P, C::kTile, t->d_items, (RaggedItem *)t->d_ritems, mask);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP, EARLY>;
+    using C = RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1>;
+    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP, EARLY, K>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRaggedThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
@@ -86,10 +82,9 @@ cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t 
                          : OP == kRagRay ? t->d_cmp_ray
                          : OP == kRagFp64 ? (const float4 *)t->d_cmp_g64
                          : EXACT ? t->d_fpad : t->d_coefp;
-    k<<<per_sm * t->num_sms, kRaggedThreads, C::kSmem, s>>>(t->d_poly, rows, t->d_ipad, pts,
-                                                            (const RaggedItem *)t->d_ritems, t->d_items, t->P,
-                                                            t->d_work, mask, t->d_queue, t->d_keys, t->d_qcount,
-                                                            t->d_error);
+    k<<<per_sm * t->num_sms, kRaggedThreads, C::kSmem, s>>>(t->d_poly, rows, t->d_ipad, pts, M, poffs, t->P,
+                                                            (BatchCounters *)t->d_batch_ctr, mask, t->d_queue,
+                                                            t->d_keys, t->d_qcount, t->d_worst, t->d_error);
     return cudaGetLastError();
 }
 
@@ -98,34 +93,38 @@ cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, c
                               uint32_t *mask, cudaStream_t s)
 {
     switch (t->batch_variant) {
-    case 1: return launch_ragged_tma_one<16, 2, INT, EXACT>(t, pts, M, poffs, mask, s);
-    case 2: return launch_ragged_tma_one<12, 3, INT, EXACT>(t, pts, M, poffs, mask, s);
-    case 3: return launch_ragged_tma_one<12, 4, INT, EXACT>(t, pts, M, poffs, mask, s);
-    default: return launch_ragged_tma_one<16, 3, INT, EXACT>(t, pts, M, poffs, mask, s);
+    case 1: return launch_ragged_tma_one<16, 3, INT, EXACT, kRagVoronoi, false, 2>(t, pts, M, poffs, mask, s);
+    case 2: return launch_ragged_tma_one<16, 3, INT, EXACT, kRagVoronoi, false, 4>(t, pts, M, poffs, mask, s);
+    case 3: return launch_ragged_tma_one<16, 2, INT, EXACT, kRagVoronoi, false, 2>(t, pts, M, poffs, mask, s);
+    case 4: return launch_ragged_tma_one<12, 3, INT, EXACT, kRagVoronoi, false, 2>(t, pts, M, poffs, mask, s);
+    case 5: return launch_ragged_tma_one<12, 4, INT, EXACT, kRagVoronoi, false, 2>(t, pts, M, poffs, mask, s);
+    default: return launch_ragged_tma_one<16, 3, INT, EXACT, kRagVoronoi, false, 1>(t, pts, M, poffs, mask, s);
     }
+}
+
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP, bool EARLY, int K>
+cudaError_t set_one_ragged_attr()
+{
+    return cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP, EARLY, K>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1>::kSmem);
+}
+
+template <int PPL, int STAGES, int K>
+cudaError_t set_ragged_attr()
+{
+    cudaError_t e = set_one_ragged_attr<PPL, STAGES, false, false, kRagVoronoi, false, K>();
+    if (e == cudaSuccess) e = set_one_ragged_attr<PPL, STAGES, true, false, kRagVoronoi, false, K>();
+    if (e == cudaSuccess) e = set_one_ragged_attr<PPL, STAGES, true, true, kRagVoronoi, false, K>();
+    return e;
 }
 
 template <int OP>
 cudaError_t set_ragged_cmp_attr()
 {
-    return cudaFuncSetAttribute(ragged_tma_kernel<16, 3, false, false, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)RaggedCfg<16, 3, OP == kRagRay ? 2 : 1>::kSmem);
+    return set_one_ragged_attr<16, 3, false, false, OP, false, 2>();
 }
 
-template <int PPL, int STAGES>
-cudaError_t set_ragged_attr()
-{
-    const int bytes = (int)RaggedCfg<PPL, STAGES>::kSmem;
-    cudaError_t e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, false, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, true, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, true, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
-}
 
 // ---------------------------------------------------------------------------
 // All pairs, split over point tiles and polygon ranges.  Each thread keeps
@@ -426,16 +425,14 @@ namespace pip {
 
 cudaError_t ragged_kernels_setup()
 {
-    cudaError_t e = set_ragged_attr<16, 3>();
-    if (e == cudaSuccess) e = set_ragged_attr<16, 2>();
-    if (e == cudaSuccess) e = set_ragged_attr<12, 3>();
-    if (e == cudaSuccess) e = set_ragged_attr<12, 4>();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ragged_tma_kernel<16, 3, false, false, kRagVoronoi, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RaggedCfg<16, 3>::kSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ragged_tma_kernel<16, 3, true, false, kRagVoronoi, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RaggedCfg<16, 3>::kSmem);
+    cudaError_t e = set_ragged_attr<16, 3, 1>();
+    if (e == cudaSuccess) e = set_ragged_attr<16, 3, 2>();
+    if (e == cudaSuccess) e = set_ragged_attr<16, 3, 4>();
+    if (e == cudaSuccess) e = set_ragged_attr<16, 2, 2>();
+    if (e == cudaSuccess) e = set_ragged_attr<12, 3, 2>();
+    if (e == cudaSuccess) e = set_ragged_attr<12, 4, 2>();
+    if (e == cudaSuccess) e = set_one_ragged_attr<16, 3, false, false, kRagVoronoi, true, 2>();
+    if (e == cudaSuccess) e = set_one_ragged_attr<16, 3, true, false, kRagVoronoi, true, 2>();
     if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagSign>();
     if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagRay>();
     if (e == cudaSuccess) e = set_ragged_cmp_attr<kRagFp64>();
@@ -446,9 +443,9 @@ cudaError_t launch_ragged_cmp(const pip_tables *t, const float *pts, int64_t M, 
                               int op, cudaStream_t s)
 {
     // one tile shape: 16 points per lane, 3 stages
-    if (op == kRagSign) return launch_ragged_tma_one<16, 3, false, false, kRagSign>(t, pts, M, poffs, mask, s);
-    if (op == kRagRay) return launch_ragged_tma_one<16, 3, false, false, kRagRay>(t, pts, M, poffs, mask, s);
-    return launch_ragged_tma_one<16, 3, false, false, kRagFp64>(t, pts, M, poffs, mask, s);
+    if (op == kRagSign) return launch_ragged_tma_one<16, 3, false, false, kRagSign, false, 2>(t, pts, M, poffs, mask, s);
+    if (op == kRagRay) return launch_ragged_tma_one<16, 3, false, false, kRagRay, false, 2>(t, pts, M, poffs, mask, s);
+    return launch_ragged_tma_one<16, 3, false, false, kRagFp64, false, 2>(t, pts, M, poffs, mask, s);
 }
 
 cudaError_t allpairs_setup()
@@ -521,10 +518,10 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
             return PIP_OK;
         }
         if (v16 && early)  // the early-exit form at the default tile shape
-            e = ints ? launch_ragged_tma_one<16, 3, true, false, kRagVoronoi, true>(t, d_points, num_points,
-                                                                                  d_point_offsets, mask, s)
-                     : launch_ragged_tma_one<16, 3, false, false, kRagVoronoi, true>(t, d_points, num_points,
-                                                                                   d_point_offsets, mask, s);
+            e = ints ? launch_ragged_tma_one<16, 3, true, false, kRagVoronoi, true, 2>(t, d_points, num_points,
+                                                                                     d_point_offsets, mask, s)
+                     : launch_ragged_tma_one<16, 3, false, false, kRagVoronoi, true, 2>(t, d_points, num_points,
+                                                                                      d_point_offsets, mask, s);
         else if (v16)  // bulk copies want a 16-byte aligned point array
             e = ints ? launch_ragged_tma<true, false>(t, d_points, num_points, d_point_offsets, mask, s)
                      : launch_ragged_tma<false, false>(t, d_points, num_points, d_point_offsets, mask, s);
