@@ -194,6 +194,28 @@ def test_every_stream_variant_matches_the_oracle_and_autotune_picks_one(n):
     t.close()
 
 
+def test_every_stream_variant_at_many_tiles_per_cta():
+    # enough points that every CTA of the one-polygon kernel streams many
+    # tiles (more than any variant's L2 prefetch distance) and ends on a
+    # ragged, odd tail
+    w = wl.vehicle_footprint(m=12_000_001)
+    want = oracle_par.inside_exact(w.vertices, w.points)
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                      max_points=w.num_points)
+    p = torch.from_numpy(w.points).to(dev())
+    mbuf, mask = guarded((w.num_points + 31) // 32)
+    for var in range(B.pip_stream_variant_count()):
+        B.pip_set_stream_variant(t, var)
+        mask.fill_(-1)
+        B.pip_test(t, p, mask=mask)
+        st, _ = B.pip_get_status(t)
+        assert st == B.PIP_OK
+        check_guards(mbuf)
+        got = np.unpackbits(mask.cpu().numpy().view(np.uint8), bitorder="little")[:w.num_points]
+        assert_same(got, want, "stream variant %d, 12,000,001 points" % var)
+    t.close()
+
+
 @pytest.mark.parametrize("ints", [False, True])
 def test_every_batch_variant_matches_the_oracle_and_autotune_picks_one(ints):
     w = (wl.integer_hulls(seed=20, num_polygons=24, points_per_polygon=2000) if ints
