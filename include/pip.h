@@ -57,7 +57,7 @@ typedef enum {
 typedef enum { PIP_F32 = 0, PIP_I32 = 1 } pip_dtype;
 
 /* pip_test output selection (bit flags) */
-enum { PIP_MASK = 1, PIP_FIRST_HIT = 2, PIP_CULL = 4, PIP_EARLY_EXIT = 8 };
+enum { PIP_MASK = 1, PIP_FIRST_HIT = 2, PIP_CULL = 4, PIP_EARLY_EXIT = 8, PIP_DISC = 16 };
 
 /* Opaque: device tables built from a batch of polygons (generators,
  * coefficients, bounds, validation results) plus the refine workspace. */
@@ -141,6 +141,22 @@ pip_status pip_prepare_p0(const void *d_vertices, pip_dtype vdtype, const int32_
  *                     decided outside.  Same results, less work; not the
  *                     full-work convention either.  Ignored by the exact
  *                     integer batch path and the all-pairs test.
+ *                     PIP_DISC may be added for one polygon (16-byte aligned
+ *                     points; not together with PIP_EARLY_EXIT, which is
+ *                     PIP_E_INVALID_ARG): in the Voronoi picture the polygon
+ *                     is the cell of p0 (Eq. 1), which holds the disc about
+ *                     p0 of half the distance to the nearest generator (the
+ *                     distance to the nearest edge line, Eq. 8) and lies in
+ *                     the disc about p0 through its farthest vertex.  The
+ *                     kernel takes both discs about o = float32(p0) (radii:
+ *                     the least distance from o to an edge line, the largest
+ *                     to a vertex), with float32 thresholds on |p - o|^2
+ *                     that cover its rounding (pip_export_tables' h_disc): a
+ *                     point inside the inner disc is decided inside, one
+ *                     outside the outer disc outside, without their edges;
+ *                     the others take the full test (filter, exact refine).
+ *                     Same results, less work; not the full-work convention.
+ *                     Ignored by the batch and all-pairs tests.
  *   d_mask            device uint32 [ceil(num_points / 32)]; bit (i % 32) of
  *                     word (i / 32) is 1 when point i is inside its polygon
  *                     (own-polygon batch) or inside at least one polygon
@@ -224,9 +240,15 @@ pip_status pip_get_polygon_status(const pip_tables *t, int32_t *h_status, void *
  *   h_origin float [num_polygons][2]    o = float32(p0)
  *   h_bound  float [num_polygons][2]    (beta0, beta1): |error of s_k| <=
  *                                       beta0 + beta1 * max(|x|, |y|)
+ *   h_disc   float [num_polygons][2]    (tin, tout), the disc bounds of
+ *                                       PIP_DISC on d2 = fl(x x + fl(y y)),
+ *                                       x = float32(p - o): d2 < tin only
+ *                                       strictly inside, d2 > tout only
+ *                                       strictly outside; (0, -inf) for an
+ *                                       invalid polygon
  */
 pip_status pip_export_tables(const pip_tables *t, double *h_g0, double *h_gk, float *h_coef,
-                             float *h_origin, float *h_bound, void *stream);
+                             float *h_origin, float *h_bound, float *h_disc, void *stream);
 
 /* Releases the tables (synchronizes the device first).  NULL is a no-op. */
 void pip_destroy(pip_tables *t);

@@ -33,6 +33,7 @@ PIP_P0_CENTROID = 0
 PIP_P0_VERTEX_MEAN = 1
 PIP_P0_GIVEN = 2
 PIP_EARLY_EXIT = 8  # one polygon / batch: warp-uniform early break over spread edges (same results)
+PIP_DISC = 16  # one polygon: points decided by the inner / outer discs about the origin skip their edges (same results)
 
 # every symbol include/pip.h declares, with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -46,7 +47,7 @@ SIGNATURES = {
     "pip_margin": (_INT, [_P, _P, _INT, _I64, _P, _P, _P]),
     "pip_get_status": (_INT, [_P, _P, ctypes.POINTER(_I64)]),
     "pip_get_polygon_status": (_INT, [_P, _P, _P]),
-    "pip_export_tables": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
+    "pip_export_tables": (_INT, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "pip_destroy": (None, [_P]),
     "pip_timing": (_INT, [_P, _INT]),
     "pip_timing_read": (_INT, [_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
@@ -328,10 +329,11 @@ def pip_export_tables(tables: Tables, stream=None) -> dict:
     coef = np.zeros((V, 4), np.float32)
     origin = np.zeros((P, 2), np.float32)
     bound = np.zeros((P, 2), np.float32)
+    disc = np.zeros((P, 2), np.float32)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    _check(lib().pip_export_tables(tables, ptr(g0), ptr(gk), ptr(coef), ptr(origin), ptr(bound),
+    _check(lib().pip_export_tables(tables, ptr(g0), ptr(gk), ptr(coef), ptr(origin), ptr(bound), ptr(disc),
                                    _stream(stream)), "pip_export_tables")
-    return {"g0": g0, "gk": gk, "coef": coef, "origin": origin, "bound": bound}
+    return {"g0": g0, "gk": gk, "coef": coef, "origin": origin, "bound": bound, "disc": disc}
 
 
 def _cmp(fn: str, tables: Tables, points: torch.Tensor, point_offsets=None, mask=None, stream=None):

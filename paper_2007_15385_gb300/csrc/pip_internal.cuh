@@ -37,7 +37,12 @@ struct PolyInfo {
     int32_t orient;      // +1 counter-clockwise, -1 clockwise, 0 invalid
     float bbox[4];       // xmin, ymin, xmax, ymax
     double gerr;         // per-coordinate bound on |stored p_k - exact mirror of stored p0|
-    double pad;
+    // Disc bounds about o, on the computed d2 = fl(x x + fl(y y)) of the local
+    // coordinates: d2 < tin only inside the largest disc about o within the
+    // polygon (strictly inside), d2 > tout only outside the smallest disc about
+    // o holding every vertex (strictly outside); tin = 0, tout = -inf when the
+    // polygon is invalid
+    float tin, tout;
 };
 static_assert(sizeof(PolyInfo) == 64, "PolyInfo is 64 bytes");
 
@@ -161,11 +166,12 @@ cudaError_t stream_kernels_setup();
 cudaError_t ragged_kernels_setup();
 cudaError_t allpairs_setup();
 int stream_variant_count();
-// the pipelined single-polygon test (pip_stream.cu): one launch, refine inline
+// the pipelined single-polygon test (pip_stream.cu): one launch, refine inline;
+// `early` the warp-uniform early break, `disc` the disc filter
 cudaError_t launch_stream_pipelined(const pip_tables *t, const void *pts, bool ints, int64_t M, uint32_t *mask, bool early,
-                                    cudaStream_t s);
+                                    bool disc, cudaStream_t s);
 cudaError_t launch_stream_pipelined_i32(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, bool early,
-                                        cudaStream_t s);
+                                        bool disc, cudaStream_t s);
 cudaError_t stream_kernels_setup_i32();
 // pip_tuning.cu: the autotuners' JSON cache (no-ops while no cache file is set)
 std::string tuning_key(const pip_tables *t, const char *kernel, int64_t num_points, int pdtype);

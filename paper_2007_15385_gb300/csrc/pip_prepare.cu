@@ -371,7 +371,7 @@ pip_status pip_get_polygon_status(const pip_tables *t, int32_t *h_status, void *
 }
 
 pip_status pip_export_tables(const pip_tables *t, double *h_g0, double *h_gk, float *h_coef,
-                             float *h_origin, float *h_bound, void *stream)
+                             float *h_origin, float *h_bound, float *h_disc, void *stream)
 {
     pip_status st = check_tables(t);
     if (st != PIP_OK) return st;
@@ -380,7 +380,7 @@ pip_status pip_export_tables(const pip_tables *t, double *h_g0, double *h_gk, fl
     if (h_g0) PIP_CUDA_TRY(cudaMemcpy(h_g0, t->d_g0, P * sizeof(double2), cudaMemcpyDeviceToHost));
     if (h_gk) PIP_CUDA_TRY(cudaMemcpy(h_gk, t->d_gk, V * sizeof(double2), cudaMemcpyDeviceToHost));
     if (h_coef) PIP_CUDA_TRY(cudaMemcpy(h_coef, t->d_coef, V * sizeof(float4), cudaMemcpyDeviceToHost));
-    if (h_origin || h_bound) {
+    if (h_origin || h_bound || h_disc) {
         PolyInfo *tmp = (PolyInfo *)malloc(P * sizeof(PolyInfo));
         if (tmp == nullptr) return PIP_E_CUDA;
         if (cudaMemcpy(tmp, t->d_poly, P * sizeof(PolyInfo), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -390,6 +390,7 @@ pip_status pip_export_tables(const pip_tables *t, double *h_g0, double *h_gk, fl
         for (size_t j = 0; j < P; ++j) {
             if (h_origin) { h_origin[2 * j] = tmp[j].ox; h_origin[2 * j + 1] = tmp[j].oy; }
             if (h_bound) { h_bound[2 * j] = tmp[j].beta0; h_bound[2 * j + 1] = tmp[j].beta1; }
+            if (h_disc) { h_disc[2 * j] = tmp[j].tin; h_disc[2 * j + 1] = tmp[j].tout; }
         }
         free(tmp);
     }

@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(
     info.bbox[1] = bb[1];
     info.bbox[2] = bb[2];
     info.bbox[3] = bb[3];
-    info.pad = 0.0;
+    info.tin = 0.f;
+    info.tout = -INFINITY;
 
     if (status != PIP_OK) {
         // an invalid polygon contains nothing: s_k = -inf for its slots
@@ -262,6 +263,32 @@ __global__ void __launch_bounds__(256) prepare_kernel(
     w1 = (float)warp_max((double)w1);
     A = warp_max(A);
 
+    // Disc bounds about o.  Outer: R^2 = max_k |v_k - o|^2 (v_k - o exact in
+    // fp64: both are float32 values relative to the shift).  Inner: r = min_k
+    // dist(o, edge line k), less the fp64 rounding of the line's value at o;
+    // r <= 0 (o on or outside an edge line after rounding) leaves no inner disc.
+    double R2 = 0.0, rin = INFINITY;
+#pragma unroll
+    for (int slot = 0; slot < 2; ++slot) {
+        const int k = lane + 32 * slot;
+        if (k >= n) continue;
+        const int km = k == 0 ? n - 1 : k - 1;
+        double xm, ym, xk, yk;
+        load_vertex(verts, vdtype, voff + km, xm, ym);
+        load_vertex(verts, vdtype, voff + k, xk, yk);
+        xm -= sx; ym -= sy; xk -= sx; yk -= sy;
+        const double vx = xk - olx, vy = yk - oly;
+        R2 = fmax(R2, vx * vx + vy * vy);
+        const double a = yk - ym, b = xm - xk;  // exact: differences of float32 values
+        // L(o) = a (o - v_k)_x + b (o - v_k)_y, the line through v_k; inside: -sigma L > 0
+        const double L = a * (olx - xk) + b * (oly - yk);
+        const double eL = ldexp(fabs(a) * (fabs(olx) + fabs(xk)) + fabs(b) * (fabs(oly) + fabs(yk)), -49);
+        const double d = (-sigma * L - eL) / (sqrt(a * a + b * b) * (1.0 + ldexp(1.0, -48)));
+        rin = fmin(rin, d);
+    }
+    R2 = warp_max(R2);
+    rin = warp_min(rin);
+
     if (lane == 0) {
         // Error bound of the float32 test, |computed s_k - exact s_k| <= B:
         // FMA chain 2.01u(|t| + |w|_1 |x|_inf), point rounding u |w|_1 |x|_inf,
@@ -278,6 +305,13 @@ __global__ void __launch_bounds__(256) prepare_kernel(
         info.beta0 = round_up_f32(b0);
         info.beta1 = round_up_f32(b1);
         info.gerr = E + ldexp(A, -51);
+        // The kernels' d2 = fl(x x + fl(y y)) of x = fl(p - o) (or of p
+        // itself when o = 0) lies within (1 +- u)^4 of the exact |p - o|^2
+        // (normal range); 16u of slack, directed rounding of the thresholds,
+        // and no inner disc at or below 2^-100 (subnormal squares)
+        const double tin = rin > 0.0 ? rin * rin * (1.0 - 16.0 * u) : 0.0;
+        info.tin = tin > ldexp(1.0, -100) ? __double2float_rd(tin) : 0.f;
+        info.tout = R2 > ldexp(1.0, -100) ? round_up_f32(R2 * (1.0 + 16.0 * u)) : INFINITY;
         poly[j] = info;
         g0_out[j] = make_double2(g0ax, g0ay);
     }

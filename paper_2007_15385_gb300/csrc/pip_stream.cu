@@ -29,7 +29,8 @@ cudaError_t launch_cmp_one(const pip_tables *t, const float *pts, int64_t M, uin
     sp.ox = sp.oy = sp.b0 = sp.b1 = 0.f;
     sp.ok = hp.status == PIP_OK;
     sp.n = sp.ok ? hp.n : 1;
-    sp.pad0 = sp.pad1 = 0;
+    sp.tin = 0.f;
+    sp.tout = -INFINITY;
     const float qnan = std::numeric_limits<float>::quiet_NaN();
     for (int e = 0; e < kParamEdges; ++e) {
         float4 c = make_float4(0.f, 0.f, qnan, 0.f), y = make_float4(qnan, qnan, 0.f, 0.f);
@@ -104,10 +105,10 @@ cudaError_t launch_cmp_stream(const pip_tables *t, const float *pts, int64_t M, 
 int stream_variant_count() { return kNumStreamVariants; }
 
 cudaError_t launch_stream_pipelined(const pip_tables *t, const void *pts, bool ints, int64_t M, uint32_t *mask,
-                                    bool early, cudaStream_t s)
+                                    bool early, bool disc, cudaStream_t s)
 {
-    return ints ? launch_stream_pipelined_i32(t, pts, M, mask, early, s)
-                : launch_stream_type<false>(t, pts, M, mask, early, s);
+    return ints ? launch_stream_pipelined_i32(t, pts, M, mask, early, disc, s)
+                : launch_stream_type<false>(t, pts, M, mask, early, disc, s);
 }
 
 }  // namespace pip

@@ -7,9 +7,9 @@ namespace pip {
 cudaError_t stream_kernels_setup_i32() { return setup_stream_type<true>(); }
 
 cudaError_t launch_stream_pipelined_i32(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask,
-                                        bool early, cudaStream_t s)
+                                        bool early, bool disc, cudaStream_t s)
 {
-    return launch_stream_type<true>(t, pts, M, mask, early, s);
+    return launch_stream_type<true>(t, pts, M, mask, early, disc, s);
 }
 
 }  // namespace pip

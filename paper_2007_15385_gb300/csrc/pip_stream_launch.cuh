@@ -20,11 +20,11 @@ struct StreamVariant {
 constexpr StreamVariant kStreamVariants[] = {{16, 3}, {16, 2}, {8, 4}, {8, 6}};
 constexpr int kNumStreamVariants = sizeof(kStreamVariants) / sizeof(kStreamVariants[0]);
 
-template <int NE, int PPL, int STAGES, bool INT, bool EARLY = false>
+template <int NE, int PPL, int STAGES, bool INT, bool EARLY = false, bool DISC = false>
 cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
 {
-    using C = StreamCfg<PPL, STAGES>;
-    auto k = stream_tma_kernel<NE, PPL, STAGES, INT, kTmaVoronoi, EARLY>;
+    using C = StreamCfg<PPL, STAGES, DISC>;
+    auto k = stream_tma_kernel<NE, PPL, STAGES, INT, kTmaVoronoi, EARLY, DISC>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStreamThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
@@ -40,7 +40,8 @@ cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint
     sp.b1 = hp.beta1;
     sp.ok = hp.status == PIP_OK;
     sp.n = sp.ok ? hp.n : 1;
-    sp.pad0 = sp.pad1 = 0;
+    sp.tin = sp.ok ? hp.tin : 0.f;
+    sp.tout = sp.ok ? hp.tout : -INFINITY;
     for (int k = 0; k < kParamEdges; ++k) {
         float4 c = make_float4(0.f, 0.f, INFINITY, 0.f);
         if (!sp.ok) { if (k == 0) c.z = -INFINITY; }
@@ -55,45 +56,46 @@ cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint
     return cudaGetLastError();
 }
 
-template <int PPL, int STAGES, bool INT, bool EARLY = false>
+template <int PPL, int STAGES, bool INT, bool EARLY = false, bool DISC = false>
 cudaError_t launch_tma_ne(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
 {
     // the polygon's edge count is known on the host from the vertex count
     const int n = t->V;
-    if (n <= 4) return launch_tma_one<4, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
-    if (n <= 8) return launch_tma_one<8, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
-    if (n <= 12) return launch_tma_one<12, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
-    if (n <= 16) return launch_tma_one<16, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
-    return launch_tma_one<0, PPL, STAGES, INT, EARLY>(t, pts, M, mask, s);
+    if (n <= 4) return launch_tma_one<4, PPL, STAGES, INT, EARLY, DISC>(t, pts, M, mask, s);
+    if (n <= 8) return launch_tma_one<8, PPL, STAGES, INT, EARLY, DISC>(t, pts, M, mask, s);
+    if (n <= 12) return launch_tma_one<12, PPL, STAGES, INT, EARLY, DISC>(t, pts, M, mask, s);
+    if (n <= 16) return launch_tma_one<16, PPL, STAGES, INT, EARLY, DISC>(t, pts, M, mask, s);
+    return launch_tma_one<0, PPL, STAGES, INT, EARLY, DISC>(t, pts, M, mask, s);
 }
 
-template <int NE, int PPL, int STAGES, bool INT, bool EARLY = false>
+template <int NE, int PPL, int STAGES, bool INT, bool EARLY = false, bool DISC = false>
 cudaError_t set_attr_one()
 {
-    return cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, INT, kTmaVoronoi, EARLY>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StreamCfg<PPL, STAGES>::kSmem);
+    return cudaFuncSetAttribute(stream_tma_kernel<NE, PPL, STAGES, INT, kTmaVoronoi, EARLY, DISC>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)StreamCfg<PPL, STAGES, DISC>::kSmem);
 }
 
-template <int PPL, int STAGES, bool INT, bool EARLY = false>
+template <int PPL, int STAGES, bool INT, bool EARLY = false, bool DISC = false>
 cudaError_t set_smem_attr()
 {
-    cudaError_t e = set_attr_one<4, PPL, STAGES, INT, EARLY>();
-    if (e == cudaSuccess) e = set_attr_one<8, PPL, STAGES, INT, EARLY>();
-    if (e == cudaSuccess) e = set_attr_one<12, PPL, STAGES, INT, EARLY>();
-    if (e == cudaSuccess) e = set_attr_one<16, PPL, STAGES, INT, EARLY>();
-    if (e == cudaSuccess) e = set_attr_one<0, PPL, STAGES, INT, EARLY>();
+    cudaError_t e = set_attr_one<4, PPL, STAGES, INT, EARLY, DISC>();
+    if (e == cudaSuccess) e = set_attr_one<8, PPL, STAGES, INT, EARLY, DISC>();
+    if (e == cudaSuccess) e = set_attr_one<12, PPL, STAGES, INT, EARLY, DISC>();
+    if (e == cudaSuccess) e = set_attr_one<16, PPL, STAGES, INT, EARLY, DISC>();
+    if (e == cudaSuccess) e = set_attr_one<0, PPL, STAGES, INT, EARLY, DISC>();
     return e;
 }
 
-template <bool INT>
+template <bool INT, bool DISC = false>
 cudaError_t launch_stream_tma(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask,
                               cudaStream_t s)
 {
     switch (t->stream_variant) {
-    case 1: return launch_tma_ne<16, 2, INT>(t, pts, M, mask, s);
-    case 2: return launch_tma_ne<8, 4, INT>(t, pts, M, mask, s);
-    case 3: return launch_tma_ne<8, 6, INT>(t, pts, M, mask, s);
-    default: return launch_tma_ne<16, 3, INT>(t, pts, M, mask, s);
+    case 1: return launch_tma_ne<16, 2, INT, false, DISC>(t, pts, M, mask, s);
+    case 2: return launch_tma_ne<8, 4, INT, false, DISC>(t, pts, M, mask, s);
+    case 3: return launch_tma_ne<8, 6, INT, false, DISC>(t, pts, M, mask, s);
+    default: return launch_tma_ne<16, 3, INT, false, DISC>(t, pts, M, mask, s);
     }
 }
 
@@ -101,6 +103,11 @@ template <bool INT>
 cudaError_t set_all_attr()
 {
     cudaError_t e = set_smem_attr<16, 3, INT, true>();  // the early-exit mode's one tile shape
+    // the disc filter's forms of the four tile shapes
+    if (e == cudaSuccess) e = set_smem_attr<16, 3, INT, false, true>();
+    if (e == cudaSuccess) e = set_smem_attr<16, 2, INT, false, true>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 4, INT, false, true>();
+    if (e == cudaSuccess) e = set_smem_attr<8, 6, INT, false, true>();
     if (e == cudaSuccess) e = set_smem_attr<16, 3, INT>();
     if (e == cudaSuccess) e = set_smem_attr<16, 2, INT>();
     if (e == cudaSuccess) e = set_smem_attr<8, 4, INT>();
@@ -108,12 +115,14 @@ cudaError_t set_all_attr()
     return e;
 }
 
-// One point type: the pipelined kernel at the chosen tile shape; the
-// early-exit mode at the default shape (16 points per lane, 3 stages).
+// One point type: the pipelined kernel (or its disc-filter form) at the
+// chosen tile shape; the early-exit mode at the default shape (16 points per
+// lane, 3 stages).
 template <bool INT>
 cudaError_t launch_stream_type(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, bool early,
-                               cudaStream_t s)
+                               bool disc, cudaStream_t s)
 {
+    if (disc) return launch_stream_tma<INT, true>(t, pts, M, mask, s);
     if (early) return launch_tma_ne<16, 3, INT, true>(t, pts, M, mask, s);
     return launch_stream_tma<INT>(t, pts, M, mask, s);
 }

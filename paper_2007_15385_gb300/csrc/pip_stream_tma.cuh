@@ -31,14 +31,18 @@ struct StreamCounters {
 constexpr int kConsumerWarps = 8;
 constexpr int kStreamThreads = (kConsumerWarps + 1) * 32;
 
-template <int PPL, int STAGES>
+// DISC: each consumer warp also owns PPL mask words in shared memory (the
+// disc filter's inside bits of the points it sends through the full test).
+template <int PPL, int STAGES, bool DISC = false>
 struct StreamCfg {
     static constexpr int kTile = kConsumerWarps * 32 * PPL;  // points per stage
     static constexpr size_t kStageBytes = (size_t)kTile * 8;
     static constexpr size_t kCoefOff = STAGES * kStageBytes;
     static constexpr int kCoef = 2 * (kMaxEdges + 4);  // float4 (w_x, w_y, t, 0), padded to 4; ray: two per edge
     static constexpr size_t kBarOff = kCoefOff + (size_t)kCoef * 16;
-    static constexpr size_t kSmem = kBarOff + 2 * STAGES * sizeof(uint64_t);
+    static constexpr size_t kDiscOff = kBarOff + 2 * STAGES * sizeof(uint64_t);
+    static constexpr size_t kDiscWarpBytes = (size_t)PPL * 4;
+    static constexpr size_t kSmem = kDiscOff + (DISC ? kConsumerWarps * kDiscWarpBytes : 0);
     // two CTAs per SM (16 consumer warps, <= 112 registers a thread) when the
     // shared memory allows it
     static constexpr int kFit = (int)((227 * 1024) / (kSmem + 1024));
@@ -60,7 +64,8 @@ constexpr int kTmaVoronoi = 0, kTmaSign = 1, kTmaRay = 2;
 constexpr int kParamEdges = 16;
 struct StreamPoly {
     float ox, oy, b0, b1;
-    int n, ok, pad0, pad1;
+    int n, ok;
+    float tin, tout;  // the polygon's disc bounds (PolyInfo)
     float wx[kParamEdges], wy[kParamEdges], t[kParamEdges];
     float y0[kParamEdges], y1[kParamEdges];
 };
@@ -81,11 +86,15 @@ struct SliceCtx {
 // each group but the last, the warp stops when every one of its points already
 // has min s < -B, i.e. is decided outside.  The full min could only be
 // smaller, so the decisions are those of the full-work test.
+// The slice's points are read from the stage once, into registers; the warp
+// then hands the stage back (one arrive on `release`) before its edge math,
+// so that the producer refills the stage while the warp computes.
 template <int NE, int PPL, bool INT, bool CENTER, bool TAIL, bool EARLY = false>
 __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned char *stage,
                                               const void *__restrict__ pts, int64_t M, int64_t wfirst,
                                               int lane, uint32_t *__restrict__ mask, bool vec_store,
-                                              uint32_t *__restrict__ myqueue, unsigned int *s_queued)
+                                              uint32_t *__restrict__ myqueue, unsigned int *s_queued,
+                                              uint64_t *release)
 {
     const int nvalid = TAIL ? (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst)) : 32 * PPL;
     const StreamPoly &sp = *cx.sp;
@@ -119,6 +128,8 @@ __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned
         xs[q] = CENTER ? x - sp.ox : x;  // local coordinates x = p - o
         ys[q] = CENTER ? y - sp.oy : y;
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(release);
     // m = min_k s_k, NaN-propagating so that a non-finite point stays undecided;
     // three operands per min (NE is a multiple of 4)
     if (EARLY) {
@@ -233,6 +244,139 @@ __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned
     }
 }
 
+// m = min_k s_k for one point (the full test's per-edge terms, NaN-propagating).
+template <int NE>
+__device__ __forceinline__ float point_min(const SliceCtx &cx, float x, float y)
+{
+    const StreamPoly &sp = *cx.sp;
+    float m;
+    if (NE > 0) {
+        m = fmin_nan(fmaf(-x, sp.wx[0], fmaf(-y, sp.wy[0], sp.t[0])),
+                     fmaf(-x, sp.wx[1], fmaf(-y, sp.wy[1], sp.t[1])));
+#pragma unroll
+        for (int k = 2; k < (NE > 0 ? NE : 2); k += 2)
+            m = fmin3_nan(m, fmaf(-x, sp.wx[k], fmaf(-y, sp.wy[k], sp.t[k])),
+                          fmaf(-x, sp.wx[k + 1], fmaf(-y, sp.wy[k + 1], sp.t[k + 1])));
+    } else {
+        m = INFINITY;
+        for (int k = 0; k < cx.npad; k += 2) {
+            const float4 c0 = cx.cs[k], c1 = cx.cs[k + 1];
+            m = fmin3_nan(m, fmaf(-x, c0.x, fmaf(-y, c0.y, c0.z)), fmaf(-x, c1.x, fmaf(-y, c1.y, c1.z)));
+        }
+    }
+    return m;
+}
+
+// The slice with the disc filter (PIP_DISC).  In the Voronoi picture the
+// polygon is the cell of p0: no generator is nearer than p0 within half the
+// distance to the nearest one, and the cell lies inside the disc through its
+// farthest vertex.  Taken about the local origin o with rigorous float32
+// thresholds (PolyInfo::tin / tout), a point with d2 = |x|^2 < tin is inside
+// and one with d2 > tout outside, without its edges.  Each lane keeps a mask
+// of its points left between the discs (in the benchmark's footprint about
+// 1 %) and takes them one per pass through the full test of consume_slice
+// (float32 filter, uncertain points queued for the exact decision); their
+// inside bits are ORed into the warp's words in shared memory.  Decisions
+// equal full work's.
+template <int NE, int PPL, bool INT, bool CENTER, bool TAIL>
+__device__ __forceinline__ void consume_slice_disc(const SliceCtx &cx, const unsigned char *stage,
+                                                   const void *__restrict__ pts, int64_t M, int64_t wfirst,
+                                                   int lane, uint32_t *__restrict__ mask, bool vec_store,
+                                                   uint32_t *__restrict__ myqueue, unsigned int *s_queued,
+                                                   uint32_t *wwords)
+{
+    static_assert(PPL <= 32, "one mask bit per point of a lane");
+    const int nvalid = TAIL ? (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst)) : 32 * PPL;
+    const StreamPoly &sp = *cx.sp;
+    // the point at slice position r (the odd last point is not in the bulk copy)
+    auto load = [&](int r, float &x, float &y) {
+        if (TAIL && wfirst + r == M - 1 && (M & 1)) {
+            const int64_t p = M - 1;
+            if (INT) {
+                x = (float)((const int32_t *)pts)[2 * p];
+                y = (float)((const int32_t *)pts)[2 * p + 1];
+            } else {
+                x = ((const float *)pts)[2 * p];
+                y = ((const float *)pts)[2 * p + 1];
+            }
+        } else if (INT) {
+            const int2 v = ((const int2 *)stage)[r];
+            x = (float)v.x;
+            y = (float)v.y;
+        } else {
+            const float2 v = ((const float2 *)stage)[r];
+            x = v.x;
+            y = v.y;
+        }
+    };
+    uint32_t w_in[PPL];
+    uint32_t nearm = 0;  // bit q: this lane's point 32 q + lane takes the full test
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        const int r = 32 * q + lane;
+        const bool valid = !TAIL || r < nvalid;
+        float x = sp.ox, y = sp.oy;
+        if (valid) load(r, x, y);
+        // an integer point that float32 does not hold exactly takes the full test
+        const bool exact = INT ? int_exact(x, y) : true;
+        const float xl = CENTER ? x - sp.ox : x, yl = CENTER ? y - sp.oy : y;
+        const float d2 = fmaf(xl, xl, yl * yl);
+        const bool in = valid && exact && d2 < sp.tin;
+        // NaN d2 is neither in nor out: the full test decides it
+        const bool near = valid && !in && !(exact && d2 > sp.tout);
+        w_in[q] = __ballot_sync(0xffffffffu, in);
+        nearm |= (uint32_t)near << q;
+    }
+    if (__any_sync(0xffffffffu, nearm != 0u)) {
+        if (lane < PPL) wwords[lane] = 0u;
+        __syncwarp();
+        const uint32_t lt = (1u << lane) - 1u;
+        while (__any_sync(0xffffffffu, nearm != 0u)) {
+            // each lane takes its lowest pending point
+            const bool act = nearm != 0u;
+            const int q = act ? __ffs(nearm) - 1 : 0;
+            nearm &= nearm - 1u;
+            const int r = 32 * q + lane;
+            float x = sp.ox, y = sp.oy;
+            if (act) load(r, x, y);
+            const bool exin = INT ? int_exact(x, y) : true;
+            const float xl = CENTER ? x - sp.ox : x, yl = CENTER ? y - sp.oy : y;
+            const float m = point_min<NE>(cx, xl, yl);
+            const float B = fmaf(sp.b1, fabsf(xl) + fabsf(yl), sp.b0);
+            const bool in = act && m >= B && exin;
+            const bool unc = act && (!(fabsf(m) >= B) || !exin);
+            if (in) atomicOr(&wwords[q], 1u << lane);
+            const uint32_t u = __ballot_sync(0xffffffffu, unc);
+            if (u) {
+                unsigned int at = 0;
+                if (lane == 0) at = atomicAdd(s_queued, (unsigned int)__popc(u));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (unc) myqueue[at + __popc(u & lt)] = (uint32_t)(wfirst + r);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) w_in[q] |= wwords[q];
+        __syncwarp();  // the words are rewritten by the next slice
+    }
+    // the slice's mask words: PPL consecutive words
+    uint32_t *mw = mask + (wfirst >> 5);
+    if (!TAIL && vec_store && (PPL % 4) == 0) {
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < PPL; q += 4)
+                *(uint4 *)(mw + q) = make_uint4(w_in[q], w_in[q + 1], w_in[q + 2], w_in[q + 3]);
+        }
+    } else {
+        const int nw = (nvalid + 31) >> 5;
+        uint32_t myword = 0;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            if (lane == q) myword = w_in[q];
+        if (lane < nw) mw[lane] = myword;
+    }
+}
+
 // The comparators' slice (float32 points, absolute coordinates as in the
 // listings): v_k = LHS_k - RHS_k = t_k - x w_kx - y w_ky per edge.  Sign of
 // offset: inside when every D_k = (v_k < 0) is the same, i.e. min v >= 0 or
@@ -241,10 +385,11 @@ __device__ __forceinline__ void consume_slice(const SliceCtx &cx, const unsigned
 // (y_{k-1} > y differs from y_k > y) and the signed v_k > 0; an odd count is
 // inside.  NE > 0: coefficients from the launch parameters, else from shared
 // memory (ray: (w_x, w_y, t, 0) and (y0, y1, 0, 0) per edge).
+// Like consume_slice, the stage is handed back once the points are in registers.
 template <int OP, int NE, int PPL, bool TAIL>
 __device__ __forceinline__ void consume_slice_cmp(const SliceCtx &cx, const unsigned char *stage,
                                                   const void *__restrict__ pts, int64_t M, int64_t wfirst, int lane,
-                                                  uint32_t *__restrict__ mask, bool vec_store)
+                                                  uint32_t *__restrict__ mask, bool vec_store, uint64_t *release)
 {
     const int nvalid = TAIL ? (int)max((int64_t)0, min((int64_t)32 * PPL, M - wfirst)) : 32 * PPL;
     const StreamPoly &sp = *cx.sp;
@@ -266,6 +411,8 @@ __device__ __forceinline__ void consume_slice_cmp(const SliceCtx &cx, const unsi
         xs[q] = x;
         ys[q] = y;
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(release);
     bool in[PPL];
     if (OP == kTmaSign) {
         float mn[PPL], mx[PPL];
@@ -350,15 +497,16 @@ __device__ __forceinline__ void consume_slice_cmp(const SliceCtx &cx, const unsi
 // registers; NE == 0: any edge count, coefficients read from shared memory.
 // OP: the Voronoi test (with its exact refine) or a comparator (no refine;
 // `coef` is then the polygon's comparator row, padded with NaN).
-template <int NE, int PPL, int STAGES, bool INT, int OP = kTmaVoronoi, bool EARLY = false>
-__global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBlocks) stream_tma_kernel(
+// DISC: the disc filter of consume_slice_disc (the Voronoi test only).
+template <int NE, int PPL, int STAGES, bool INT, int OP = kTmaVoronoi, bool EARLY = false, bool DISC = false>
+__global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES, DISC>::kMinBlocks) stream_tma_kernel(
     const __grid_constant__ StreamPoly sp, const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
     const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab,
     const void *__restrict__ verts, int vdtype, const void *__restrict__ pts, int64_t M,
     uint32_t *__restrict__ mask, uint32_t *__restrict__ queue, StreamCounters *__restrict__ ctr,
     unsigned int *__restrict__ last_refine, int *__restrict__ err)
 {
-    using C = StreamCfg<PPL, STAGES>;
+    using C = StreamCfg<PPL, STAGES, DISC>;
     constexpr int kTile = C::kTile;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *cs = (float4 *)(smem + C::kCoefOff);
@@ -446,24 +594,41 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES>::kMinBl
             if (!mbar_wait(&full[s], fphase, err)) break;
             const unsigned char *stage = smem + (size_t)s * C::kStageBytes + (size_t)warp * 32 * PPL * 8;
             const bool whole = wfirst + 32 * PPL <= whole_end;
-            if (OP != kTmaVoronoi) {
+            if (DISC && OP == kTmaVoronoi) {
+                uint32_t *wwords = (uint32_t *)(smem + C::kDiscOff + (size_t)warp * C::kDiscWarpBytes);
+                if (whole) {
+                    if (center)
+                        consume_slice_disc<NE, PPL, INT, true, false>(cx, stage, pts, M, wfirst, lane, mask,
+                                                                     vec_store, myqueue, &s_refined, wwords);
+                    else
+                        consume_slice_disc<NE, PPL, INT, false, false>(cx, stage, pts, M, wfirst, lane, mask,
+                                                                      vec_store, myqueue, &s_refined, wwords);
+                } else {
+                    consume_slice_disc<NE, PPL, INT, true, true>(cx, stage, pts, M, wfirst, lane, mask, vec_store,
+                                                                myqueue, &s_refined, wwords);
+                }
+                // the near pass reads the stage again: hand it back afterwards
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            } else if (OP != kTmaVoronoi) {
+                // these hand the stage back themselves, once the points are in registers
                 if (whole)
-                    consume_slice_cmp<OP, NE, PPL, false>(cx, stage, pts, M, wfirst, lane, mask, vec_store);
+                    consume_slice_cmp<OP, NE, PPL, false>(cx, stage, pts, M, wfirst, lane, mask, vec_store,
+                                                          &empty[s]);
                 else
-                    consume_slice_cmp<OP, NE, PPL, true>(cx, stage, pts, M, wfirst, lane, mask, vec_store);
+                    consume_slice_cmp<OP, NE, PPL, true>(cx, stage, pts, M, wfirst, lane, mask, vec_store,
+                                                         &empty[s]);
             } else if (whole) {
                 if (center)
                     consume_slice<NE, PPL, INT, true, false, EARLY>(cx, stage, pts, M, wfirst, lane, mask,
-                                                                   vec_store, myqueue, &s_refined);
+                                                                   vec_store, myqueue, &s_refined, &empty[s]);
                 else
                     consume_slice<NE, PPL, INT, false, false, EARLY>(cx, stage, pts, M, wfirst, lane, mask,
-                                                                    vec_store, myqueue, &s_refined);
+                                                                    vec_store, myqueue, &s_refined, &empty[s]);
             } else {
                 consume_slice<NE, PPL, INT, true, true, EARLY>(cx, stage, pts, M, wfirst, lane, mask,
-                                                              vec_store, myqueue, &s_refined);
+                                                              vec_store, myqueue, &s_refined, &empty[s]);
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
             if (++s == STAGES) {
                 s = 0;
                 fphase ^= 1u;

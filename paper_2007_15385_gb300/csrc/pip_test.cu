@@ -476,9 +476,11 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     if (pdtype != PIP_F32 && pdtype != PIP_I32) return PIP_E_INVALID_ARG;
     if (num_points < 0) return PIP_E_INVALID_ARG;
     if (num_points > t->capacity) return PIP_E_CAPACITY;
-    if ((mode & ~(PIP_MASK | PIP_FIRST_HIT | PIP_CULL | PIP_EARLY_EXIT)) || !(mode & (PIP_MASK | PIP_FIRST_HIT)))
+    if ((mode & ~(PIP_MASK | PIP_FIRST_HIT | PIP_CULL | PIP_EARLY_EXIT | PIP_DISC)) || !(mode & (PIP_MASK | PIP_FIRST_HIT)))
         return PIP_E_INVALID_ARG;
     const bool early = (mode & PIP_EARLY_EXIT) != 0;
+    const bool disc = (mode & PIP_DISC) != 0;
+    if (early && disc) return PIP_E_INVALID_ARG;
     const bool want_mask = mode & PIP_MASK, want_hit = mode & PIP_FIRST_HIT;
     if (want_hit && d_point_offsets != nullptr) return PIP_E_INVALID_ARG;
     if (num_points == 0) {  // nothing to decide; the refine count of this call is 0
@@ -531,7 +533,7 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
     } else if (t->P == 1 && !want_hit && v16 && t->have_host_poly) {
         // the pipelined kernel: bulk test and exact refine in one launch
         timing_mark(t, 0, s);
-        e = launch_stream_pipelined(t, d_points, ints, num_points, mask, early, s);
+        e = launch_stream_pipelined(t, d_points, ints, num_points, mask, early, disc, s);
         if (e != cudaSuccess) return PIP_E_CUDA;
         timing_mark(t, 1, s);
         timing_mark(t, 2, s);

@@ -76,7 +76,7 @@ def test_host_argument_checks_of_the_other_entry_points(lib):
     assert lib.pip_timing(None, 1) == B.PIP_E_INVALID_ARG
     assert lib.pip_timing_read(None, ctypes.byref(i32), ctypes.byref(f64), ctypes.byref(f64)) == B.PIP_E_INVALID_ARG
     assert lib.pip_get_polygon_status(None, None, None) == B.PIP_E_INVALID_ARG
-    assert lib.pip_export_tables(None, None, None, None, None, None, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_export_tables(None, None, None, None, None, None, None, None) == B.PIP_E_INVALID_ARG
     assert lib.pip_set_stream_variant(None, 0) == B.PIP_E_INVALID_ARG
     assert lib.pip_set_batch_variant(None, 0) == B.PIP_E_INVALID_ARG
     assert lib.pip_autotune_stream(None, None, 0, 1, None, 1, None, ctypes.byref(i32),

@@ -817,6 +817,127 @@ def test_early_exit_equals_full_work_and_the_oracle():
         t.close()
 
 
+def _sliver(seed, width):
+    # a thin triangle 500 long at coordinates ~1e3 (float32 ulp 6e-5): the
+    # thinner ones put o = float32(p0) within ulps of the long edges
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-1e3, 1e3, 2)
+    d = rng.normal(size=2)
+    d /= np.linalg.norm(d)
+    v = np.array([a, a + 500.0 * d, a + 250.0 * d + width * np.array([-d[1], d[0]])], np.float32)
+    return v
+
+
+def test_disc_bounds_hold_exactly():
+    """The disc thresholds, in exact rationals: tout >= R^2 (1 + u)^4 with R
+    the largest distance from o to a vertex, and tin <= r^2 (1 - u)^4 with r
+    the least distance from o to an edge line, o strictly inside (tin > 0);
+    (1 +- u)^4 bounds the kernels' rounding of d2 = fl(x x + fl(y y)) of
+    x = fl(p - o).  Invalid polygons hold (0, -inf)."""
+    from fractions import Fraction as Fr
+    u = Fr(1, 1 << 24)
+    polys = [wl.vehicle_footprint(seed=60, m=2), wl.gis_batch(seed=61, num_polygons=300, m_range=(1, 2)),
+             wl.integer_hulls(seed=62, num_polygons=60, points_per_polygon=2)]
+    sl = [_sliver(70 + i, wd) for i, wd in enumerate((1e-2, 3e-3, 1e-3, 3e-4, 2e-4, 1e-4, 1e-4, 1e-4))]
+    polys.append(wl.Workload("slivers", np.concatenate(sl), np.arange(0, 3 * len(sl) + 1, 3, dtype=np.int32),
+                             np.zeros((1, 2), np.float32)))
+    polys.append(wl.Workload("invalid", np.array([[0, 0], [1, 0], [2, 0], [0, 0], [1, 1], [0, 1]], np.float32),
+                             np.array([0, 3, 6], np.int32), np.zeros((1, 2), np.float32)))
+    seen_inner = seen_no_inner = 0
+    for w in polys:
+        t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                          max_points=1)
+        ex = B.pip_export_tables(t)
+        status = B.pip_get_polygon_status(t)
+        t.close()
+        for j in range(w.num_polygons):
+            tin, tout = (float(x) for x in ex["disc"][j])
+            if status[j] != B.PIP_OK:
+                assert tin == 0.0 and tout == -math.inf
+                continue
+            vv = [(Fr(float(x)), Fr(float(y))) for x, y in w.vertices[w.vertex_offsets[j]:w.vertex_offsets[j + 1]]]
+            ox, oy = Fr(float(ex["origin"][j][0])), Fr(float(ex["origin"][j][1]))
+            R2 = max((x - ox) ** 2 + (y - oy) ** 2 for x, y in vv)
+            assert Fr(tout) >= R2 * (1 + u) ** 4, (w.name, j)
+            if tin == 0.0:
+                seen_no_inner += 1
+                continue
+            seen_inner += 1
+            area2 = sum(vv[k - 1][0] * vv[k][1] - vv[k][0] * vv[k - 1][1] for k in range(len(vv)))
+            sigma = 1 if area2 > 0 else -1
+            for k in range(len(vv)):
+                (xm, ym), (xk, yk) = vv[k - 1], vv[k]
+                a, b = yk - ym, xm - xk
+                L = a * (ox - xk) + b * (oy - yk)
+                assert -sigma * L > 0, (w.name, j, k)
+                assert Fr(tin) <= L * L / (a * a + b * b) * (1 - u) ** 4, (w.name, j, k)
+    assert seen_inner > 300
+
+
+def _disc_points(w, rng):
+    """The workload's points plus points at the two thresholds' radii (a few
+    ulps either side, many directions), o itself, the vertices, edge
+    midpoints and non-finite or huge coordinates."""
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                      max_points=1)
+    ex = B.pip_export_tables(t)
+    t.close()
+    o = ex["origin"][0].astype(np.float64)
+    tin, tout = (float(x) for x in ex["disc"][0])
+    th = rng.uniform(0, 2 * np.pi, 4096)
+    extra = [w.points.astype(np.float32)]
+    for T in (tin, tout):
+        if T > 0 and np.isfinite(T):
+            for f in (1 - 8e-7, 1 - 1e-7, 1.0, 1 + 1e-7, 1 + 8e-7):
+                r = math.sqrt(T) * f
+                extra.append(np.stack([o[0] + r * np.cos(th), o[1] + r * np.sin(th)], 1).astype(np.float32))
+    v = w.vertices.astype(np.float64)
+    extra.append(v.astype(np.float32))
+    extra.append(((v + np.roll(v, -1, 0)) / 2).astype(np.float32))
+    extra.append(np.array([o, [np.nan, 0], [0, np.inf], [-np.inf, 1], [1e30, -1e30], [3e38, 3e38]], np.float32))
+    pts = np.concatenate(extra).astype(np.float32)
+    return wl.Workload(w.name, w.vertices, w.vertex_offsets, rng.permutation(pts))
+
+
+def _disc_cases():
+    rng = np.random.default_rng(57)
+    yield "footprint, 12 edges", _disc_points(wl.vehicle_footprint(seed=58, m=1_000_003), rng)
+    for n in (3, 5, 8, 16, 17, 40, 64):
+        yield "%d-gon" % n, _disc_points(wl.unit_circle_octagon(seed=310 + n, m=200_001, n=n), rng)
+    far = wl.unit_circle_octagon(seed=330, m=300_001, n=12)
+    far = wl.Workload("off origin", far.vertices * 3.0 + np.float32(5000.0), far.vertex_offsets,
+                      far.points * 3.0 + np.float32(5000.0))
+    yield "12-gon away from the origin", _disc_points(far, rng)
+    yield "sliver", _disc_points(wl.Workload("sliver", _sliver(80, 1e-2), np.array([0, 3], np.int32),
+                                             rng.uniform(-1e3, 1e3, (300_001, 2)).astype(np.float32)), rng)
+    hull = wl.integer_hulls(seed=59, num_polygons=1, points_per_polygon=300_001)
+    pts = hull.points.copy()
+    pts[::97] = rng.integers(-(1 << 30), 1 << 30, size=pts[::97].shape)  # beyond float32's exact integers
+    yield "integer points", wl.Workload("h", hull.vertices.astype(np.float32), hull.vertex_offsets, pts)
+
+
+def test_disc_filter_equals_full_work_and_the_oracle():
+    """PIP_DISC decides the points inside the inner disc or outside the outer
+    one without their edges; the masks must be those of the full-work test
+    and of the oracle, at and around both thresholds and on the odd tail."""
+    for name, w in _disc_cases():
+        v = torch.from_numpy(w.vertices).to(dev())
+        vo = torch.from_numpy(w.vertex_offsets).to(dev())
+        p = torch.from_numpy(np.ascontiguousarray(w.points)).to(dev())
+        t = B.pip_prepare(v, vo, max_points=w.num_points)
+        full, _ = B.pip_test(t, p)
+        disc, _ = B.pip_test(t, p, mode=B.PIP_MASK | B.PIP_DISC)
+        st, _ = B.pip_get_status(t)
+        assert st == B.PIP_OK
+        got_full = B.unpack_mask(full, w.num_points).cpu().numpy()
+        got_disc = B.unpack_mask(disc, w.num_points).cpu().numpy()
+        assert_same(got_disc, got_full, name + ": disc filter vs full work")
+        assert_same(got_disc, oracle_own(w), name + ": disc filter vs the oracle")
+        with pytest.raises(RuntimeError):
+            B.pip_test(t, p, mode=B.PIP_MASK | B.PIP_DISC | B.PIP_EARLY_EXIT)
+        t.close()
+
+
 @pytest.mark.parametrize("kind", ["centroid", "vertex_mean", "chebyshev"])
 def test_inner_generator_choices_give_the_oracle_masks(kind):
     """Any interior point may be p0 (Sec. 3): with the vertex mean or the
@@ -980,6 +1101,18 @@ def test_vehicle_footprint_full_size_every_point():
     got, _, refine, st = run_test(w)
     assert st == B.PIP_OK
     assert_same(got, oracle_par.inside_exact(w.vertices, w.points), "footprint, all 2^26 points")
+
+
+def test_vehicle_footprint_disc_filter_full_size_every_point():
+    w = wl.vehicle_footprint()
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                      max_points=w.num_points)
+    mask, _ = B.pip_test(t, torch.from_numpy(w.points).to(dev()), mode=B.PIP_MASK | B.PIP_DISC)
+    st, _ = B.pip_get_status(t)
+    assert st == B.PIP_OK
+    got = B.unpack_mask(mask, w.num_points).cpu().numpy()
+    t.close()
+    assert_same(got, oracle_par.inside_exact(w.vertices, w.points), "footprint with the disc filter, all 2^26 points")
 
 
 def test_gis_batch_full_size_every_point():
