@@ -441,14 +441,7 @@ def main():
     dcalls, dbulk_ms, _ = B.pip_timing_read(t)
     B.pip_timing(t, False)
     dk_ms = dbulk_ms / max(1, dcalls)
-    ex = B.pip_export_tables(t)
-    o = ex["origin"][0]
-    tin, tout = (float(x) for x in ex["disc"][0])
-    xl = w.points[:, 0] - o[0] if o[0] or o[1] else w.points[:, 0]
-    yl = w.points[:, 1] - o[1] if o[0] or o[1] else w.points[:, 1]
-    d2 = xl * xl + yl * yl
-    full_frac = float(np.count_nonzero((d2 >= tin) & (d2 <= tout))) / M
-    del xl, yl, d2
+    full_frac = disc_full_fraction(B, t, w)
     disc = {"ms_per_step": dms, "effective_Gtests_per_s": tests_per_step / (dms * 1e-3) / 1e9,
             "kernel_ms": dk_ms,
             "roofline": {"bound": "hbm", "achieved": bytes_per_launch / (dk_ms * 1e-3) / 1e9, "peak": peak,
@@ -810,6 +803,20 @@ def workload_cpu_baseline(name: str, w) -> dict:
 WORKLOADS = ("unit_circle_octagon", "gis_batch", "gis_all_pairs", "integer_hulls", "footprint_trajectory")
 
 
+def disc_full_fraction(B, t, w) -> float:
+    """Share of the points between the disc filter's two discs (they take the
+    full test), counted on the host from the exported thresholds with the
+    kernels' float32 d2 (output formatting only)."""
+    ex = B.pip_export_tables(t)
+    offs = w.point_offsets if w.point_offsets is not None else np.array([0, len(w.points)])
+    between = 0
+    for j in range(len(offs) - 1):
+        q = w.points[offs[j]:offs[j + 1]].astype(np.float32) - ex["origin"][j]
+        d2 = q[:, 0] * q[:, 0] + q[:, 1] * q[:, 1]
+        between += int(np.count_nonzero((d2 >= ex["disc"][j][0]) & (d2 <= ex["disc"][j][1])))
+    return between / max(1, len(w.points))
+
+
 def bench_workload(name: str, B, wl, dev, stream, steps: int, warmup: int, fma_peak: dict | None,
                    sm_mhz: float, polygons: int = 0, with_cpu: bool = True) -> dict:
     """Every measurement of one workload other than the headline: the call's
@@ -885,6 +892,29 @@ def bench_workload(name: str, B, wl, dev, stream, steps: int, warmup: int, fma_p
             ems = time_steps(ecall, steps, 3, stream)
             out["early_exit"] = {"ms_per_step": ems, "effective_Gtests_per_s": tests / (ems * 1e-3) / 1e9,
                                  "note": "PIP_EARLY_EXIT: a warp stops once all its points are decided outside"}
+        if name in ("gis_batch", "unit_circle_octagon"):
+            # the disc filter (PIP_DISC): same results, less work, reported
+            # apart as an effective rate with its kernel's HBM roofline
+            dcall = lambda: B.pip_test(t, p, po, mode=mode | B.PIP_DISC, mask=mask, first_hit=hit)
+            dms = time_steps(dcall, steps, 3, stream)
+            B.pip_timing(t, True)
+            for _ in range(steps):
+                dcall()
+            dcalls, dbulk_ms, drefine_ms = B.pip_timing_read(t)
+            B.pip_timing(t, False)
+            dk = dbulk_ms / max(1, dcalls)
+            peak, kind = measured_peaks()
+            nbytes = M * 8 + ((M + 31) // 32) * 4
+            out["disc_filter"] = {"ms_per_step": dms, "effective_Gtests_per_s": tests / (dms * 1e-3) / 1e9,
+                                  "bulk_kernel_ms": dk, "refine_kernel_ms": drefine_ms / max(1, dcalls),
+                                  "roofline": {"bound": "hbm", "achieved": nbytes / (dk * 1e-3) / 1e9,
+                                               "peak": peak, "unit": "GB/s",
+                                               "frac": nbytes / (dk * 1e-3) / 1e9 / peak,
+                                               "peak_kind": kind + " hbm_gbs",
+                                               "call_frac": nbytes / (dms * 1e-3) / 1e9 / peak},
+                                  "full_test_fraction": disc_full_fraction(B, t, w),
+                                  "note": "PIP_DISC: points inside the inner or outside the outer disc about o "
+                                          "skip their edges (full_test_fraction: the points between the discs)"}
         if name == "gis_all_pairs":
             # bounding-box cull and early stop (PIP_CULL): same results, less work;
             # reported apart as an effective rate, not as the full-work value

@@ -141,8 +141,9 @@ pip_status pip_prepare_p0(const void *d_vertices, pip_dtype vdtype, const int32_
  *                     decided outside.  Same results, less work; not the
  *                     full-work convention either.  Ignored by the exact
  *                     integer batch path and the all-pairs test.
- *                     PIP_DISC may be added for one polygon (16-byte aligned
- *                     points; not together with PIP_EARLY_EXIT, which is
+ *                     PIP_DISC may be added for one polygon or an
+ *                     own-polygon batch (16-byte aligned points; not
+ *                     together with PIP_EARLY_EXIT, which is
  *                     PIP_E_INVALID_ARG): in the Voronoi picture the polygon
  *                     is the cell of p0 (Eq. 1), which holds the disc about
  *                     p0 of half the distance to the nearest generator (the
@@ -156,7 +157,8 @@ pip_status pip_prepare_p0(const void *d_vertices, pip_dtype vdtype, const int32_
  *                     outside the outer disc outside, without their edges;
  *                     the others take the full test (filter, exact refine).
  *                     Same results, less work; not the full-work convention.
- *                     Ignored by the batch and all-pairs tests.
+ *                     Ignored by the exact integer batch path (integer
+ *                     polygons with integer points) and the all-pairs test.
  *   d_mask            device uint32 [ceil(num_points / 32)]; bit (i % 32) of
  *                     word (i / 32) is 1 when point i is inside its polygon
  *                     (own-polygon batch) or inside at least one polygon

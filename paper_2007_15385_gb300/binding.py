@@ -33,7 +33,7 @@ PIP_P0_CENTROID = 0
 PIP_P0_VERTEX_MEAN = 1
 PIP_P0_GIVEN = 2
 PIP_EARLY_EXIT = 8  # one polygon / batch: warp-uniform early break over spread edges (same results)
-PIP_DISC = 16  # one polygon: points decided by the inner / outer discs about the origin skip their edges (same results)
+PIP_DISC = 16  # one polygon / batch: points decided by the inner / outer discs about the origin skip their edges (same results)
 
 # every symbol include/pip.h declares, with (restype, argtypes)
 _P = ctypes.c_void_p

@@ -53,7 +53,9 @@ struct RaggedHeader {
 
 // K: polygons per stage (1, 2 or 4).  ROWS: 16-byte entries per edge of a
 // staged polygon row (2 for the ray comparator, 1 otherwise).
-template <int PPL, int STAGES, int K = 1, int ROWS = 1>
+// DISC: each consumer warp also owns, in shared memory, PPL mask words and a
+// list of up to 32 * PPL slice positions (the disc filter's undecided points).
+template <int PPL, int STAGES, int K = 1, int ROWS = 1, bool DISC = false>
 struct RaggedCfg {
     static constexpr int kSlice = 32 * PPL;
     static constexpr int kTile = kRaggedWarps * kSlice;  // points per chunk
@@ -64,10 +66,16 @@ struct RaggedCfg {
     static constexpr size_t kHdrOff = kInfoOff + K * sizeof(PolyInfo);
     static constexpr size_t kStageBytes = (kHdrOff + sizeof(RaggedHeader) + 127) & ~(size_t)127;
     static constexpr size_t kBarOff = STAGES * kStageBytes;
-    static constexpr size_t kSmem = kBarOff + 2 * STAGES * sizeof(uint64_t);
+    static constexpr size_t kDiscOff = kBarOff + 2 * STAGES * sizeof(uint64_t);
+    static constexpr size_t kDiscWarpBytes = (size_t)PPL * 4 + (size_t)kSlice * 2;
+    static constexpr size_t kSmem = kDiscOff + (DISC ? kRaggedWarps * kDiscWarpBytes : 0);
     static constexpr int kFit = (int)((227 * 1024) / (kSmem + 1024));
     static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
 };
+
+// The disc filter pays where the full test costs more per point than the
+// filter's pass: polygons of at least this many edges (fewer take full work).
+constexpr int kDiscMinEdges = 8;
 
 // The batch kernel's counters, zero between launches: the next chunk, the
 // refine queue's fill, the CTAs that have finished.
@@ -298,6 +306,139 @@ __device__ __forceinline__ void ragged_slice(const float4 *cs, int n, float ox, 
     ragged_store_words<PPL, TAIL>(w_in, gs, a, b, bw, lane, mask, vec_store);
 }
 
+// m = min_k s_k for two points against a staged row: four edges a step, two
+// partial minima per point so that the min chains stay short (NaN-propagating).
+__device__ __forceinline__ void ragged_point_min2(const float4 *cs, int n, float x0, float y0, float x1, float y1,
+                                                  float &m0, float &m1)
+{
+    float a0 = INFINITY, b0 = INFINITY, a1 = INFINITY, b1 = INFINITY;
+    int k = 0;
+#pragma unroll 2
+    for (; k + 4 <= n; k += 4) {
+        const float4 c0 = cs[k], c1 = cs[k + 1], c2 = cs[k + 2], c3 = cs[k + 3];
+        a0 = fmin3_nan(a0, fmaf(-x0, c0.x, fmaf(-y0, c0.y, c0.z)), fmaf(-x0, c1.x, fmaf(-y0, c1.y, c1.z)));
+        b0 = fmin3_nan(b0, fmaf(-x0, c2.x, fmaf(-y0, c2.y, c2.z)), fmaf(-x0, c3.x, fmaf(-y0, c3.y, c3.z)));
+        a1 = fmin3_nan(a1, fmaf(-x1, c0.x, fmaf(-y1, c0.y, c0.z)), fmaf(-x1, c1.x, fmaf(-y1, c1.y, c1.z)));
+        b1 = fmin3_nan(b1, fmaf(-x1, c2.x, fmaf(-y1, c2.y, c2.z)), fmaf(-x1, c3.x, fmaf(-y1, c3.y, c3.z)));
+    }
+    for (; k < n; ++k) {
+        const float4 c0 = cs[k];
+        a0 = fmin_nan(a0, fmaf(-x0, c0.x, fmaf(-y0, c0.y, c0.z)));
+        a1 = fmin_nan(a1, fmaf(-x1, c0.x, fmaf(-y1, c0.y, c0.z)));
+    }
+    m0 = fmin_nan(a0, b0);
+    m1 = fmin_nan(a1, b1);
+}
+
+// The disc filter (PIP_DISC) in a batch slice, as consume_slice_disc of the
+// one-polygon kernel with the polygon's own thresholds (PolyInfo::tin /
+// tout): a point with d2 = |p - o|^2 < tin is inside, one with d2 > tout
+// outside, without its edges.  The rest are listed per warp in shared memory
+// (`wlist`) and decided 64 at a time, two per lane, by the full test
+// (ragged_point_min2, the float32 bound, uncertain points queued with their
+// polygon); their inside bits are ORed into the warp's words (`wwords`).
+template <int PPL, bool INT, bool CENTER, bool TAIL>
+__device__ __forceinline__ void ragged_slice_disc(const float4 *cs, const PolyInfo &pi, const unsigned char *rows,
+                                                  const void *__restrict__ pts, int64_t gs, int64_t a, int64_t b,
+                                                  int64_t bw, int lane, uint32_t *__restrict__ mask, bool vec_store,
+                                                  int j, uint32_t *__restrict__ queue, uint32_t *__restrict__ qpoly,
+                                                  unsigned int *__restrict__ qcount, uint32_t *wwords,
+                                                  uint16_t *wlist)
+{
+    const float ox = pi.ox, oy = pi.oy;
+    // point gs + r; an integer point that float32 does not hold exactly
+    // becomes NaN, so that the full test leaves it to the exact refine
+    auto load = [&](int r, float &x, float &y) {
+        const int64_t p = gs + r;
+        if (TAIL && p == b - 1 && (b & 1)) {
+            if (INT) {
+                x = (float)((const int32_t *)pts)[2 * p];
+                y = (float)((const int32_t *)pts)[2 * p + 1];
+            } else {
+                x = ((const float *)pts)[2 * p];
+                y = ((const float *)pts)[2 * p + 1];
+            }
+        } else if (INT) {
+            const int2 v = ((const int2 *)rows)[r];
+            x = (float)v.x;
+            y = (float)v.y;
+        } else {
+            const float2 v = ((const float2 *)rows)[r];
+            x = v.x;
+            y = v.y;
+        }
+        if (INT && !int_exact(x, y)) x = __int_as_float(0x7fc00000);
+    };
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t w_in[PPL], nb[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        const int r = 32 * q + lane;
+        const int64_t p = gs + r;
+        const bool valid = !TAIL || (p >= a && p < b);
+        float x = ox, y = oy;
+        if (valid) load(r, x, y);
+        const float xl = CENTER ? x - ox : x, yl = CENTER ? y - oy : y;
+        const float d2 = fmaf(xl, xl, yl * yl);
+        const bool in = valid && d2 < pi.tin;
+        const bool near = valid && !in && !(d2 > pi.tout);  // NaN: the full test
+        w_in[q] = __ballot_sync(0xffffffffu, in);
+        nb[q] = __ballot_sync(0xffffffffu, near);
+    }
+    // the list: positions from the ballots alone, so the writes do not wait
+    // on one another
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        if ((nb[q] >> lane) & 1u) wlist[cnt + __popc(nb[q] & lt)] = (uint16_t)(32 * q + lane);
+        cnt += __popc(nb[q]);
+    }
+    if (cnt) {  // warp-uniform
+        uint32_t myword = 0;
+#pragma unroll
+        for (int q = 0; q < PPL; ++q)
+            if (lane == q) myword = w_in[q];
+        if (lane < PPL) wwords[lane] = myword;
+        __syncwarp();
+        for (int base = 0; base < cnt; base += 64) {
+            const bool act0 = base + lane < cnt, act1 = base + 32 + lane < cnt;
+            const int r0 = act0 ? wlist[base + lane] : 0, r1 = act1 ? wlist[base + 32 + lane] : 0;
+            float x0 = ox, y0 = oy, x1 = ox, y1 = oy;
+            if (act0) load(r0, x0, y0);
+            if (act1) load(r1, x1, y1);
+            const float xl0 = CENTER ? x0 - ox : x0, yl0 = CENTER ? y0 - oy : y0;
+            const float xl1 = CENTER ? x1 - ox : x1, yl1 = CENTER ? y1 - oy : y1;
+            float m0, m1;
+            ragged_point_min2(cs, pi.n, xl0, yl0, xl1, yl1, m0, m1);
+            const float B0 = fmaf(pi.beta1, fabsf(xl0) + fabsf(yl0), pi.beta0);
+            const float B1 = fmaf(pi.beta1, fabsf(xl1) + fabsf(yl1), pi.beta0);
+            if (act0 && m0 >= B0) atomicOr(&wwords[r0 >> 5], 1u << (r0 & 31));
+            if (act1 && m1 >= B1) atomicOr(&wwords[r1 >> 5], 1u << (r1 & 31));
+            const bool unc0 = act0 && !(fabsf(m0) >= B0), unc1 = act1 && !(fabsf(m1) >= B1);
+            const uint32_t u0 = __ballot_sync(0xffffffffu, unc0), u1 = __ballot_sync(0xffffffffu, unc1);
+            if (u0 | u1) {
+                unsigned int at = 0;
+                if (lane == 0) at = atomicAdd(qcount, (unsigned int)(__popc(u0) + __popc(u1)));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (unc0) {
+                    queue[at + __popc(u0 & lt)] = (uint32_t)(gs + r0);
+                    qpoly[at + __popc(u0 & lt)] = (uint32_t)j;
+                }
+                at += __popc(u0);
+                if (unc1) {
+                    queue[at + __popc(u1 & lt)] = (uint32_t)(gs + r1);
+                    qpoly[at + __popc(u1 & lt)] = (uint32_t)j;
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) w_in[q] = wwords[q];
+        __syncwarp();  // the words and the list are rewritten by the next slice
+    }
+    ragged_store_words<PPL, TAIL>(w_in, gs, a, b, bw, lane, mask, vec_store);
+}
+
 // Integer polygon and integer points, decided exactly here: no filter, no
 // queue, no refine.  Edge k of the staged row is (a_x, a_y, e_x, e_y) in
 // float32, a = v_{k-1}, e = orient (v_k - v_{k-1}); p is inside (closed) iff
@@ -508,16 +649,18 @@ __device__ __forceinline__ void ragged_slice_empty(int64_t gs, int64_t a, int64_
 // polygons beyond +-2^22.  OP other than kRagVoronoi: a comparator, `coefp`
 // its row table (float polygons and points), nothing queued.  K: polygons per
 // stage.  `qcount` receives the number of queued points (the refine's count).
-template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false, int K = 1>
+// DISC: the disc filter of ragged_slice_disc (float Voronoi test only).
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false, int K = 1,
+          bool DISC = false>
 __global__ void __launch_bounds__(kRaggedThreads,
-                                  RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1>::kMinBlocks) ragged_tma_kernel(
+                                  RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1, DISC>::kMinBlocks) ragged_tma_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, const int4 *__restrict__ ipad,
     const void *__restrict__ pts, int64_t M, const int64_t *__restrict__ poffs, int P,
     BatchCounters *__restrict__ ctr, uint32_t *__restrict__ mask, uint32_t *__restrict__ queue,
     uint32_t *__restrict__ qpoly, unsigned int *__restrict__ qcount, int32_t *__restrict__ worst,
     int *__restrict__ err)
 {
-    using C = RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1>;
+    using C = RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1, DISC>;
     constexpr int kSlice = C::kSlice;
     constexpr int kTile = C::kTile;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -727,6 +870,22 @@ __global__ void __launch_bounds__(kRaggedThreads,
                         else
                             ragged_slice_exact<PPL, true>(cs, irow, pi.n, poly_small, rows, pts, gs, a, b, bw, lane,
                                                           mask, vec_store);
+                    } else if (DISC && pi.n >= kDiscMinEdges) {
+                        unsigned char *dw = smem + C::kDiscOff + (size_t)(warp * C::kDiscWarpBytes);
+                        uint32_t *wwords = (uint32_t *)dw;
+                        uint16_t *wlist = (uint16_t *)(dw + PPL * 4);
+                        if (!whole)
+                            ragged_slice_disc<PPL, INT, true, true>(cs, pi, rows, pts, gs, a, b, bw, lane, mask,
+                                                                    vec_store, j, queue, qpoly, &ctr->qfill, wwords,
+                                                                    wlist);
+                        else if (pi.ox == 0.f && pi.oy == 0.f)
+                            ragged_slice_disc<PPL, INT, false, false>(cs, pi, rows, pts, gs, a, b, bw, lane, mask,
+                                                                      vec_store, j, queue, qpoly, &ctr->qfill, wwords,
+                                                                      wlist);
+                        else
+                            ragged_slice_disc<PPL, INT, true, false>(cs, pi, rows, pts, gs, a, b, bw, lane, mask,
+                                                                     vec_store, j, queue, qpoly, &ctr->qfill, wwords,
+                                                                     wlist);
                     } else if (whole) {
                         if (pi.ox == 0.f && pi.oy == 0.f)
                             ragged_slice<PPL, INT, false, false, EARLY>(cs, pi.n, 0.f, 0.f, pi.beta0, pi.beta1, rows,

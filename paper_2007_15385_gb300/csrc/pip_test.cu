@@ -65,12 +65,13 @@ struct BatchVariant {
 constexpr BatchVariant kBatchVariants[] = {{16, 3, 1}, {16, 3, 2}, {16, 3, 4}, {16, 2, 2}, {12, 3, 2}, {12, 4, 2}};
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false, int K = 1>
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP = kRagVoronoi, bool EARLY = false, int K = 1,
+          bool DISC = false>
 cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
                                   uint32_t *mask, cudaStream_t s)
 {
-    using C = RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1>;
-    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP, EARLY, K>;
+    using C = RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1, DISC>;
+    auto k = ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP, EARLY, K, DISC>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRaggedThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
@@ -88,26 +89,28 @@ cudaError_t launch_ragged_tma_one(const pip_tables *t, const void *pts, int64_t 
     return cudaGetLastError();
 }
 
-template <bool INT, bool EXACT>
+// DISC: the disc-filter form of the chosen tile shape (float polygons).
+template <bool INT, bool EXACT, bool DISC = false>
 cudaError_t launch_ragged_tma(const pip_tables *t, const void *pts, int64_t M, const int64_t *poffs,
                               uint32_t *mask, cudaStream_t s)
 {
+    constexpr int V = kRagVoronoi;
     switch (t->batch_variant) {
-    case 1: return launch_ragged_tma_one<16, 3, INT, EXACT, kRagVoronoi, false, 2>(t, pts, M, poffs, mask, s);
-    case 2: return launch_ragged_tma_one<16, 3, INT, EXACT, kRagVoronoi, false, 4>(t, pts, M, poffs, mask, s);
-    case 3: return launch_ragged_tma_one<16, 2, INT, EXACT, kRagVoronoi, false, 2>(t, pts, M, poffs, mask, s);
-    case 4: return launch_ragged_tma_one<12, 3, INT, EXACT, kRagVoronoi, false, 2>(t, pts, M, poffs, mask, s);
-    case 5: return launch_ragged_tma_one<12, 4, INT, EXACT, kRagVoronoi, false, 2>(t, pts, M, poffs, mask, s);
-    default: return launch_ragged_tma_one<16, 3, INT, EXACT, kRagVoronoi, false, 1>(t, pts, M, poffs, mask, s);
+    case 1: return launch_ragged_tma_one<16, 3, INT, EXACT, V, false, 2, DISC>(t, pts, M, poffs, mask, s);
+    case 2: return launch_ragged_tma_one<16, 3, INT, EXACT, V, false, 4, DISC>(t, pts, M, poffs, mask, s);
+    case 3: return launch_ragged_tma_one<16, 2, INT, EXACT, V, false, 2, DISC>(t, pts, M, poffs, mask, s);
+    case 4: return launch_ragged_tma_one<12, 3, INT, EXACT, V, false, 2, DISC>(t, pts, M, poffs, mask, s);
+    case 5: return launch_ragged_tma_one<12, 4, INT, EXACT, V, false, 2, DISC>(t, pts, M, poffs, mask, s);
+    default: return launch_ragged_tma_one<16, 3, INT, EXACT, V, false, 1, DISC>(t, pts, M, poffs, mask, s);
     }
 }
 
-template <int PPL, int STAGES, bool INT, bool EXACT, int OP, bool EARLY, int K>
+template <int PPL, int STAGES, bool INT, bool EXACT, int OP, bool EARLY, int K, bool DISC = false>
 cudaError_t set_one_ragged_attr()
 {
-    return cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP, EARLY, K>,
+    return cudaFuncSetAttribute(ragged_tma_kernel<PPL, STAGES, INT, EXACT, OP, EARLY, K, DISC>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1>::kSmem);
+                                (int)RaggedCfg<PPL, STAGES, K, OP == kRagRay ? 2 : 1, DISC>::kSmem);
 }
 
 template <int PPL, int STAGES, int K>
@@ -116,6 +119,8 @@ cudaError_t set_ragged_attr()
     cudaError_t e = set_one_ragged_attr<PPL, STAGES, false, false, kRagVoronoi, false, K>();
     if (e == cudaSuccess) e = set_one_ragged_attr<PPL, STAGES, true, false, kRagVoronoi, false, K>();
     if (e == cudaSuccess) e = set_one_ragged_attr<PPL, STAGES, true, true, kRagVoronoi, false, K>();
+    if (e == cudaSuccess) e = set_one_ragged_attr<PPL, STAGES, false, false, kRagVoronoi, false, K, true>();
+    if (e == cudaSuccess) e = set_one_ragged_attr<PPL, STAGES, true, false, kRagVoronoi, false, K, true>();
     return e;
 }
 
@@ -524,6 +529,9 @@ extern "C" pip_status pip_test(const pip_tables *t, const void *d_points, pip_dt
                                                                                      d_point_offsets, mask, s)
                      : launch_ragged_tma_one<16, 3, false, false, kRagVoronoi, true, 2>(t, d_points, num_points,
                                                                                       d_point_offsets, mask, s);
+        else if (v16 && disc)  // the disc filter at the chosen tile shape
+            e = ints ? launch_ragged_tma<true, false, true>(t, d_points, num_points, d_point_offsets, mask, s)
+                     : launch_ragged_tma<false, false, true>(t, d_points, num_points, d_point_offsets, mask, s);
         else if (v16)  // bulk copies want a 16-byte aligned point array
             e = ints ? launch_ragged_tma<true, false>(t, d_points, num_points, d_point_offsets, mask, s)
                      : launch_ragged_tma<false, false>(t, d_points, num_points, d_point_offsets, mask, s);

@@ -938,6 +938,64 @@ def test_disc_filter_equals_full_work_and_the_oracle():
         t.close()
 
 
+def _batch_disc_cases():
+    rng = np.random.default_rng(61)
+    g = wl.gis_batch(seed=62, num_polygons=80, m_range=(0, 20_000))
+    yield "gis batch", g
+    # the same polygons with points on both radii of every polygon, its
+    # vertices and a few non-finite points, each polygon's own range
+    ex_t = B.pip_prepare(torch.from_numpy(g.vertices).to(dev()), torch.from_numpy(g.vertex_offsets).to(dev()),
+                         max_points=1)
+    ex = B.pip_export_tables(ex_t)
+    ex_t.close()
+    pts, offs = [], [0]
+    for j in range(g.num_polygons):
+        o = ex["origin"][j].astype(np.float64)
+        tin, tout = (float(x) for x in ex["disc"][j])
+        th = rng.uniform(0, 2 * np.pi, 300)
+        own = [g.points[g.point_offsets[j]:g.point_offsets[j + 1]]]
+        for T in (tin, tout):
+            if T > 0:
+                for f in (1 - 4e-7, 1.0, 1 + 4e-7):
+                    r = math.sqrt(T) * f
+                    own.append(np.stack([o[0] + r * np.cos(th), o[1] + r * np.sin(th)], 1).astype(np.float32))
+        own.append(g.vertices[g.vertex_offsets[j]:g.vertex_offsets[j + 1]])
+        own.append(np.array([[np.nan, o[1]], [o[0], np.inf]], np.float32))
+        q = rng.permutation(np.concatenate(own).astype(np.float32))
+        pts.append(q)
+        offs.append(offs[-1] + len(q))
+    yield "gis batch at the radii", wl.Workload("radii", g.vertices, g.vertex_offsets, np.concatenate(pts),
+                                                np.array(offs, np.int64))
+    h = wl.integer_hulls(seed=63, num_polygons=30, points_per_polygon=6_000)
+    pts = h.points.copy()
+    pts[::89] = rng.integers(-(1 << 30), 1 << 30, size=pts[::89].shape)
+    yield "integer points, float polygons", wl.Workload("hf", h.vertices.astype(np.float32), h.vertex_offsets,
+                                                        pts, h.point_offsets)
+
+
+def test_batch_disc_filter_every_variant_equals_full_work_and_the_oracle():
+    """The batch kernel's disc filter, at every tile shape: the masks of the
+    full-work test and of the oracle."""
+    for name, w in _batch_disc_cases():
+        v = torch.from_numpy(w.vertices).to(dev())
+        vo = torch.from_numpy(w.vertex_offsets).to(dev())
+        p = torch.from_numpy(np.ascontiguousarray(w.points)).to(dev())
+        po = torch.from_numpy(w.point_offsets).to(dev())
+        want = oracle_own(w)
+        t = B.pip_prepare(v, vo, max_points=w.num_points)
+        for var in range(B.pip_batch_variant_count()):
+            B.pip_set_batch_variant(t, var)
+            full, _ = B.pip_test(t, p, po)
+            disc, _ = B.pip_test(t, p, po, mode=B.PIP_MASK | B.PIP_DISC)
+            st, _ = B.pip_get_status(t)
+            assert st == B.PIP_OK
+            got_full = B.unpack_mask(full, w.num_points).cpu().numpy()
+            got_disc = B.unpack_mask(disc, w.num_points).cpu().numpy()
+            assert_same(got_disc, got_full, "%s, variant %d: disc filter vs full work" % (name, var))
+            assert_same(got_disc, want, "%s, variant %d: disc filter vs the oracle" % (name, var))
+        t.close()
+
+
 @pytest.mark.parametrize("kind", ["centroid", "vertex_mean", "chebyshev"])
 def test_inner_generator_choices_give_the_oracle_masks(kind):
     """Any interior point may be p0 (Sec. 3): with the vertex mean or the
@@ -1121,6 +1179,20 @@ def test_gis_batch_full_size_every_point():
     assert st == B.PIP_OK
     want = oracle_par.inside_exact_ragged(w.vertices, w.vertex_offsets, w.points, w.point_offsets)
     assert_same(got, want, "gis batch, all %d points" % w.num_points)
+
+
+def test_gis_batch_disc_filter_full_size_every_point():
+    w = wl.gis_batch()
+    t = B.pip_prepare(torch.from_numpy(w.vertices).to(dev()), torch.from_numpy(w.vertex_offsets).to(dev()),
+                      max_points=w.num_points)
+    mask, _ = B.pip_test(t, torch.from_numpy(w.points).to(dev()), torch.from_numpy(w.point_offsets).to(dev()),
+                         mode=B.PIP_MASK | B.PIP_DISC)
+    st, _ = B.pip_get_status(t)
+    assert st == B.PIP_OK
+    got = B.unpack_mask(mask, w.num_points).cpu().numpy()
+    t.close()
+    want = oracle_par.inside_exact_ragged(w.vertices, w.vertex_offsets, w.points, w.point_offsets)
+    assert_same(got, want, "gis batch with the disc filter, all points")
 
 
 def test_all_pairs_full_size_every_point():
