@@ -46,7 +46,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per launch of the pipelined kernel on this
 # workload, from one ncu capture of 2^25 points scaled by 2 to the 2^26-point
 # launch, valid only while the kernel sources hash to the value recorded with it.
-NCU_TRAFFIC = {"bytes": 548307968, "sources_sha": "baadea9d5eaed6f1"}
+NCU_TRAFFIC = {"bytes": 548558336, "sources_sha": "0f2d7a6b4329fa1f"}
 # GB300 HBM3e nominal bandwidth, reported beside the measured-peak fraction
 NOMINAL_HBM_GBS = 7900.0
 KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_stream_tma.cuh",
@@ -260,6 +260,8 @@ def main():
     ap.add_argument("--calls-only", action="store_true",
                     help="with --workload: prepare, then only W + K calls of the workload's main call "
                          "(no tuning, graphs, comparators or oracle; a small target for profilers)")
+    ap.add_argument("--disc", action="store_true",
+                    help="with --calls-only: the workload's call with the disc filter (PIP_DISC)")
     ap.add_argument("--headline-only", action="store_true",
                     help="time only the headline step (no per-workload objects)")
     ap.add_argument("--no-comparators", action="store_true",
@@ -984,6 +986,8 @@ def run_calls_only(args, B, wl, dev, stream):
         po = torch.from_numpy(w.point_offsets).to(dev) if w.point_offsets is not None else None
         t = B.pip_prepare(v, vo, max_points=w.num_points)
         mode = B.PIP_MASK | (B.PIP_FIRST_HIT if args.workload == "gis_all_pairs" else 0)
+        if args.disc:
+            mode |= B.PIP_DISC
         mask = torch.empty((w.num_points + 31) // 32, dtype=torch.int32, device=dev)
         hit = torch.empty(w.num_points, dtype=torch.int32, device=dev) if mode & B.PIP_FIRST_HIT else None
         call = lambda: B.pip_test(t, p, po, mode=mode, mask=mask, first_hit=hit)
