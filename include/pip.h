@@ -383,17 +383,29 @@ pip_status pip_test_voronoi_fp64(const pip_tables *t, const float *d_points,
  *   d_grad_loss  device float [1] (the upstream dL_total/dL) or NULL for 1
  *   d_grad_vertices device double [num_vertices][2];  d_grad_poses device double [num_poses][3]
  *
+ *   flags        0, or PIP_PENALTY_CULL: the pairs provably beyond 120 tau of
+ *                every edge line (a disc about the pose's centroid, from
+ *                the largest angle between consecutive edge normals and the
+ *                largest centroid-to-edge distance) are left out before
+ *                their margin is formed.  Their float32 softplus term and
+ *                gradient are exactly 0, so the results are those of the
+ *                full pass up to the order of the float32 partial sums;
+ *                less work, not the full-work timing convention.  Other
+ *                bits: PIP_E_INVALID_ARG.
+ *
  * An invalid footprint (see pip_prepare) gives loss 0 and zero gradients.
  * No host synchronisation.
  * ------------------------------------------------------------------------ */
+enum { PIP_PENALTY_CULL = 1 };
 size_t pip_penalty_workspace_bytes(int32_t num_vertices, int32_t num_poses, int64_t num_points);
 pip_status pip_penalty_forward(const float *d_vertices, int32_t num_vertices, const float *d_poses,
                                int32_t num_poses, const float *d_points, int64_t num_points, float tau,
-                               double *d_loss, void *d_workspace, size_t workspace_bytes, void *stream);
+                               double *d_loss, int32_t flags, void *d_workspace, size_t workspace_bytes,
+                               void *stream);
 pip_status pip_penalty_backward(const float *d_vertices, int32_t num_vertices, const float *d_poses,
                                 int32_t num_poses, const float *d_points, int64_t num_points, float tau,
                                 const float *d_grad_loss, double *d_grad_vertices, double *d_grad_poses,
-                                void *d_workspace, size_t workspace_bytes, void *stream);
+                                int32_t flags, void *d_workspace, size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
  * pip_test_single_noalloc -- the paper has no counterpart to this call; it

@@ -33,6 +33,7 @@ PIP_P0_CENTROID = 0
 PIP_P0_VERTEX_MEAN = 1
 PIP_P0_GIVEN = 2
 PIP_EARLY_EXIT = 8  # one polygon / batch: warp-uniform early break over spread edges (same results)
+PIP_PENALTY_CULL = 1  # penalty: pairs provably beyond 120 tau of every edge line left out (same results)
 PIP_DISC = 16  # one polygon / batch: points decided by the inner / outer discs about the origin skip their edges (same results)
 
 # every symbol include/pip.h declares, with (restype, argtypes)
@@ -72,9 +73,9 @@ SIGNATURES = {
     "pip_autotune_batch": (_INT, [_P, _P, _INT, _I64, _P, _P, _I32, _P, ctypes.POINTER(_I32),
                                   ctypes.POINTER(ctypes.c_float)]),
     "pip_penalty_workspace_bytes": (ctypes.c_size_t, [_I32, _I32, _I64]),
-    "pip_penalty_forward": (_INT, [_P, _I32, _P, _I32, _P, _I64, ctypes.c_float, _P, _P,
+    "pip_penalty_forward": (_INT, [_P, _I32, _P, _I32, _P, _I64, ctypes.c_float, _P, _I32, _P,
                                     ctypes.c_size_t, _P]),
-    "pip_penalty_backward": (_INT, [_P, _I32, _P, _I32, _P, _I64, ctypes.c_float, _P, _P, _P, _P,
+    "pip_penalty_backward": (_INT, [_P, _I32, _P, _I32, _P, _I64, ctypes.c_float, _P, _P, _P, _I32, _P,
                                      ctypes.c_size_t, _P]),
     "pip_set_stream_variant": (_INT, [_P, _I32]),
     "pip_autotune_stream": (_INT, [_P, _P, _INT, _I64, _P, _I32, _P, ctypes.POINTER(_I32),
@@ -489,8 +490,9 @@ def _penalty_ws(vertices, poses, points):
 
 
 def pip_penalty_forward(vertices: torch.Tensor, poses: torch.Tensor, points: torch.Tensor, tau: float,
-                        workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Collision penalty sum softplus(-margin/tau) over poses x points; fp64 scalar tensor."""
+                        workspace: torch.Tensor | None = None, stream=None, cull: bool = False) -> torch.Tensor:
+    """Collision penalty sum softplus(-margin/tau) over poses x points; fp64 scalar tensor.
+    cull: leave out the pairs whose terms are exactly 0 in float32 (PIP_PENALTY_CULL)."""
     for t_, nm in ((vertices, "vertices"), (poses, "poses"), (points, "points")):
         _dev(t_, nm)
         if t_.dtype != torch.float32:
@@ -499,15 +501,16 @@ def pip_penalty_forward(vertices: torch.Tensor, poses: torch.Tensor, points: tor
     loss = torch.empty(1, dtype=torch.float64, device=vertices.device)
     _check(lib().pip_penalty_forward(vertices.data_ptr(), vertices.numel() // 2, poses.data_ptr(),
                                      poses.numel() // 3, points.data_ptr(), points.numel() // 2,
-                                     float(tau), loss.data_ptr(), ws.data_ptr(), ws.numel(),
-                                     _stream(stream)), "pip_penalty_forward")
+                                     float(tau), loss.data_ptr(), PIP_PENALTY_CULL if cull else 0,
+                                     ws.data_ptr(), ws.numel(), _stream(stream)), "pip_penalty_forward")
     return loss[0]
 
 
 def pip_penalty_backward(vertices: torch.Tensor, poses: torch.Tensor, points: torch.Tensor, tau: float,
                          grad_loss: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
-                         stream=None):
-    """(d loss/d vertices [n, 2] fp64, d loss/d poses [P, 3] fp64), scaled by grad_loss."""
+                         stream=None, cull: bool = False):
+    """(d loss/d vertices [n, 2] fp64, d loss/d poses [P, 3] fp64), scaled by grad_loss.
+    cull: leave out the pairs whose gradient is exactly 0 in float32 (PIP_PENALTY_CULL)."""
     ws = workspace if workspace is not None else _penalty_ws(vertices, poses, points)
     gv = torch.empty((vertices.numel() // 2, 2), dtype=torch.float64, device=vertices.device)
     gp = torch.empty((poses.numel() // 3, 3), dtype=torch.float64, device=vertices.device)
@@ -517,31 +520,33 @@ def pip_penalty_backward(vertices: torch.Tensor, poses: torch.Tensor, points: to
     _check(lib().pip_penalty_backward(vertices.data_ptr(), vertices.numel() // 2, poses.data_ptr(),
                                       poses.numel() // 3, points.data_ptr(), points.numel() // 2,
                                       float(tau), go.data_ptr() if go is not None else None,
-                                      gv.data_ptr(), gp.data_ptr(), ws.data_ptr(), ws.numel(),
-                                      _stream(stream)), "pip_penalty_backward")
+                                      gv.data_ptr(), gp.data_ptr(), PIP_PENALTY_CULL if cull else 0,
+                                      ws.data_ptr(), ws.numel(), _stream(stream)), "pip_penalty_backward")
     return gv, gp
 
 
 class CollisionPenalty(torch.autograd.Function):
     """L = sum_pose sum_point softplus(-margin(R^T (p - t)) / tau) with hand-written CUDA
     forward and backward kernels; gradients for the footprint vertices and the poses (the
-    obstacle points are data).  The generator tables are rebuilt in backward."""
+    obstacle points are data).  The generator tables are rebuilt in backward.  cull: leave
+    out the pairs whose terms and gradients are exactly 0 in float32 (PIP_PENALTY_CULL)."""
 
     @staticmethod
-    def forward(ctx, vertices, poses, points, tau: float):
+    def forward(ctx, vertices, poses, points, tau: float, cull: bool = False):
         v = vertices.detach().contiguous()
         p = poses.detach().contiguous()
         q = points.detach().contiguous()
         ctx.save_for_backward(v, p, q)
         ctx.tau = float(tau)
-        return pip_penalty_forward(v, p, q, ctx.tau)
+        ctx.cull = bool(cull)
+        return pip_penalty_forward(v, p, q, ctx.tau, cull=ctx.cull)
 
     @staticmethod
     def backward(ctx, grad_out):
         v, p, q = ctx.saved_tensors
-        gv, gp = pip_penalty_backward(v, p, q, ctx.tau, grad_loss=grad_out)
-        return gv.to(v.dtype), gp.to(p.dtype), None, None
+        gv, gp = pip_penalty_backward(v, p, q, ctx.tau, grad_loss=grad_out, cull=ctx.cull)
+        return gv.to(v.dtype), gp.to(p.dtype), None, None, None
 
 
-def collision_penalty(vertices, poses, points, tau: float):
-    return CollisionPenalty.apply(vertices, poses, points, tau)
+def collision_penalty(vertices, poses, points, tau: float, cull: bool = False):
+    return CollisionPenalty.apply(vertices, poses, points, tau, cull)

@@ -55,7 +55,13 @@ struct PenWorkspace {
     float4 *pose_coef;  // [P][kPoseStride]  per-pose affine forms (w'_x, w'_y, c', 0), rounded
     float4 *pose_lo;    // [P][kPoseStride]  what the rounding left: exact - rounded, in float32
     double2 *pose_rot;  // [P]  (cos theta, sin theta)
+    float4 *pose_cull;  // [P]  (T_x, T_y, threshold on |p - T|^2, 0): the cull disc (PIP_PENALTY_CULL)
 };
+
+// The cull (PIP_PENALTY_CULL) leaves out the pairs whose margin is provably
+// above kCullZ tau: their float32 softplus term (e^-|z| below 2^-150) and
+// their gradient (the backward queues z >= -88 only) are exactly 0.
+constexpr double kCullZ = 120.0;
 
 constexpr int kPoseStride = kMaxEdges;
 constexpr int kRedPer = 2048;     // loss partials per first-level reduction block
@@ -87,6 +93,7 @@ size_t carve(void *base, int n, int P, int64_t blocks, PenWorkspace *w)
     w->pose_coef = (float4 *)take((size_t)P * kPoseStride * sizeof(float4));
     w->pose_lo = (float4 *)take((size_t)P * kPoseStride * sizeof(float4));
     w->pose_rot = (double2 *)take((size_t)P * sizeof(double2));
+    w->pose_cull = (float4 *)take((size_t)P * sizeof(float4));
     return off;
 }
 
@@ -156,7 +163,8 @@ __global__ void __launch_bounds__(64) pose_coef_kernel(const PolyInfo *__restric
                                                        const double2 *__restrict__ gktab,
                                                        const float *__restrict__ poses, int P,
                                                        float4 *__restrict__ pose_coef, float4 *__restrict__ pose_lo,
-                                                       double2 *__restrict__ pose_rot)
+                                                       double2 *__restrict__ pose_rot, float tau,
+                                                       float4 *__restrict__ pose_cull)
 {
     const int j = blockIdx.x, k = threadIdx.x;
     if (j >= P) return;
@@ -179,6 +187,51 @@ __global__ void __launch_bounds__(64) pose_coef_kernel(const PolyInfo *__restric
         }
         pose_coef[(size_t)j * kPoseStride + e] = r;
         pose_lo[(size_t)j * kPoseStride + e] = lo;
+    }
+    if (k == 0) {
+        // The pose's cull disc.  With w_k the unit outward normals and H the
+        // largest |p_k - p0| / 2 (the distance from p0 to an edge line), every
+        // unit direction u meets some normal within half the largest angle
+        // theta between consecutive normals, so
+        //     m(x) = max_k (w_k . (x - p0) - |p_k - p0| / 2) >= kappa |x - p0| - H,
+        // kappa = cos(theta / 2).  In world coordinates |x - p0| = |p - T|,
+        // T = t + R p0.  A pair with |p - T| > (kCullZ tau + H) / kappa has
+        // m > kCullZ tau; the threshold on the float32 d2 = fl(e_x e_x + fl(e_y e_y)),
+        // e = fl(p - float32(T)), carries 2^-20 of relative slack and 2^-20 |T|_1
+        // of absolute slack for the roundings of e, d2 and T.  No cull when a
+        // turn is pi or more (not convex) or the footprint is invalid.
+        float4 pc = make_float4(0.f, 0.f, INFINITY, 0.f);
+        if (n > 0) {
+            const double2 g0 = g0tab[0];
+            double H = 0.0, cmin = 1.0;
+            bool ok = true;
+            double2 gl = gktab[n - 1];
+            double qx = gl.x - g0.x, qy = gl.y - g0.y;
+            double ql = sqrt(qx * qx + qy * qy);
+            qx /= ql;
+            qy /= ql;
+            for (int e = 0; e < n; ++e) {
+                const double2 g = gktab[e];
+                const double ux = g.x - g0.x, uy = g.y - g0.y, D = sqrt(ux * ux + uy * uy);
+                const double wx = ux / D, wy = uy / D;
+                H = fmax(H, 0.5 * D);
+                if (!((qx * wy - qy * wx) * pi.orient > 0.0)) ok = false;
+                cmin = fmin(cmin, qx * wx + qy * wy);
+                qx = wx;
+                qy = wy;
+            }
+            const double kappa = sqrt(0.5 * (1.0 + cmin)) * (1.0 - 0x1p-40);
+            const double tx = poses[3 * j], ty = poses[3 * j + 1];
+            const double Tx = tx + cn * g0.x - sn * g0.y, Ty = ty + sn * g0.x + cn * g0.y;
+            pc.x = (float)Tx;
+            pc.y = (float)Ty;
+            if (ok && kappa > 0.0) {
+                const double R = (kCullZ * (double)tau + H) / kappa * (1.0 + 0x1p-20) +
+                                 0x1p-20 * (fabs((double)pc.x) + fabs((double)pc.y)) + 0x1p-100;
+                pc.z = __double2float_ru(R * R * (1.0 + 0x1p-20));
+            }
+        }
+        pose_cull[j] = pc;
     }
 }
 
@@ -317,12 +370,22 @@ __device__ __forceinline__ int argmax_edge_ff(const float4 *cs, const float4 *cl
 
 // The register count is left to the compiler (58 at 12 edges, 4 blocks per
 // SM): capping it at 128 or 80 measured 25 % and 14 % slower.
+// CULL: each warp first tests its pairs against the pose's cull disc
+// (pose_cull) and rings the pairs inside it in shared memory (p_x, p_y, after
+// the backward pass's arrays); those go through the pair logic 32 at a time,
+// the others add exactly 0 to the loss and nothing to the gradient.
 template <int NE, bool BACKWARD>
+constexpr size_t pen_smem(bool cull)
+{
+    return (BACKWARD ? acc_bytes<NE>() : 0) + (cull ? (size_t)(kPenThreads / 32) * 2 * kPenQueue * sizeof(float) : 0);
+}
+
+template <int NE, bool BACKWARD, bool CULL = false>
 __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ pose_coef,
     const float4 *__restrict__ pose_lo, const double2 *__restrict__ pose_rot, const float *__restrict__ poses,
     const float *__restrict__ pts, int64_t M, int nv, float tau, double *__restrict__ loss_part, double *__restrict__ pose_part,
-    double *__restrict__ edge_part)
+    double *__restrict__ edge_part, const float4 *__restrict__ pose_cull)
 {
     constexpr int kWarps = kPenThreads / 32;
     extern __shared__ float lane_acc[];  // backward: [acc_rows][kLW] accumulators, then the warps' queues
@@ -423,6 +486,41 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
             __syncwarp();  // finished slots are refilled next
         }
     };
+    // CULL: the ring of pairs inside the cull disc (holds at most 31 + 2 x 32)
+    float *cx = lane_acc + (BACKWARD ? acc_bytes<NE>() / sizeof(float) : 0) + (size_t)(threadIdx.x >> 5) * 2 * kPenQueue;
+    float *cy = cx + kPenQueue;
+    int ch = 0, ct = 0;
+    float Tx = 0.f, Ty = 0.f, Tc = INFINITY;
+    if (CULL) {
+        const float4 pc = pose_cull[pose];
+        Tx = pc.x;
+        Ty = pc.y;
+        Tc = pc.z;
+    }
+    auto cull_pair = [&](float2 pt, bool valid) {
+        const float ex = pt.x - Tx, ey = pt.y - Ty;
+        const bool in = valid && !(fmaf(ex, ex, ey * ey) > Tc);  // NaN: kept
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (bal) {
+            const int at = (ct + __popc(bal & ((1u << lane) - 1u))) & (kPenQueue - 1);
+            if (in) {
+                cx[at] = pt.x;
+                cy[at] = pt.y;
+            }
+            ct += __popc(bal);
+        }
+    };
+    // whole groups of 32 ringed pairs through the pair logic (after every second pair)
+    auto cull_drain = [&]() {
+        while (ct - ch >= 32) {
+            __syncwarp();
+            const int sl = (ch + lane) & (kPenQueue - 1);
+            const float2 pt = make_float2(cx[sl], cy[sl]);
+            ch += 32;
+            pair(pt, true);
+            if (BACKWARD) drain();
+        }
+    };
     // Steps of kStep points, kPenUnroll per thread, with the next step's
     // points loaded into the other register set while these are evaluated.
     // FULL: a whole tile of kPenPoints, no bounds checks.
@@ -439,8 +537,14 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
         auto eval = [&](int st, const float2 (&p)[kPenUnroll]) {
 #pragma unroll
             for (int u = 0; u < kPenUnroll; ++u) {
-                pair(p[u], FULL || st * kStep + u * kPenThreads + (int)threadIdx.x < cnt);
-                if (BACKWARD && (u & 1)) drain();
+                const bool valid = FULL || st * kStep + u * kPenThreads + (int)threadIdx.x < cnt;
+                if (CULL) {
+                    cull_pair(p[u], valid);
+                    if (u & 1) cull_drain();
+                } else {
+                    pair(p[u], valid);
+                    if (BACKWARD && (u & 1)) drain();
+                }
             }
         };
         float2 a[kPenUnroll], b[kPenUnroll];
@@ -456,6 +560,16 @@ __global__ void __launch_bounds__(kPenThreads) penalty_kernel(
     if (n > 0) {
         if (cnt == kPenPoints) tile(BoolTag<true>());
         else tile(BoolTag<false>());
+        if (CULL) {
+            // the last ringed pairs (fewer than 32)
+            __syncwarp();
+            const int rem = ct - ch;
+            float2 pt = make_float2(Tx, Ty);
+            if (lane < rem) pt = make_float2(cx[(ch + lane) & (kPenQueue - 1)], cy[(ch + lane) & (kPenQueue - 1)]);
+            pair(pt, lane < rem);
+            ch = ct;
+            if (BACKWARD) drain();
+        }
         if (BACKWARD) {
             __syncwarp();
             if (lane < qt - qh) finish((qh + lane) & (kPenQueue - 1));
@@ -637,22 +751,25 @@ __global__ void __launch_bounds__(64) penalty_chain_kernel(
 }
 
 // the footprint's edge count is known on the host: pick the register variant
-template <bool BACKWARD>
+template <bool BACKWARD, bool CULL>
 void launch_penalty(int n, dim3 grid, cudaStream_t s, const PenWorkspace &w, const float *poses,
                     const float *pts, int64_t M, float tau)
 {
     const int P = (int)grid.y;
-    pose_coef_kernel<<<P, 64, 0, s>>>(w.poly, w.g0, w.gk, poses, P, w.pose_coef, w.pose_lo, w.pose_rot);
-    // the backward pass's accumulators and queues (up to 57 KiB at 16 edges)
-    // with the static reduction buffers pass the default 48 KiB limit
+    pose_coef_kernel<<<P, 64, 0, s>>>(w.poly, w.g0, w.gk, poses, P, w.pose_coef, w.pose_lo, w.pose_rot, tau,
+                                      w.pose_cull);
+    // the backward pass's accumulators and queues (up to 57 KiB at 16 edges,
+    // 8 KiB more with the cull's rings) with the static reduction buffers
+    // pass the default 48 KiB limit
 #define PIP_PEN(NE)                                                                                     \
     do {                                                                                                \
+        const size_t sm = pen_smem<NE, BACKWARD>(CULL);                                                 \
         if (BACKWARD)                                                                                   \
-            cudaFuncSetAttribute(penalty_kernel<NE, BACKWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)acc_bytes<NE>());                                                 \
-        penalty_kernel<NE, BACKWARD><<<grid, kPenThreads, BACKWARD ? acc_bytes<NE>() : 0, s>>>(          \
+            cudaFuncSetAttribute(penalty_kernel<NE, BACKWARD, CULL>,                                    \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);                 \
+        penalty_kernel<NE, BACKWARD, CULL><<<grid, kPenThreads, sm, s>>>(                               \
             w.poly, w.pose_coef, w.pose_lo, w.pose_rot, poses, pts, M, n, tau, w.loss_part, w.pose_part,  \
-            w.edge_part);                                                                                 \
+            w.edge_part, w.pose_cull);                                                                    \
     } while (0)
     if (n <= 4) PIP_PEN(4);
     else if (n <= 8) PIP_PEN(8);
@@ -687,12 +804,13 @@ size_t pip_penalty_workspace_bytes(int32_t num_vertices, int32_t num_poses, int6
 
 pip_status pip_penalty_forward(const float *d_vertices, int32_t num_vertices, const float *d_poses,
                                int32_t num_poses, const float *d_points, int64_t num_points, float tau,
-                               double *d_loss, void *d_workspace, size_t workspace_bytes, void *stream)
+                               double *d_loss, int32_t flags, void *d_workspace, size_t workspace_bytes,
+                               void *stream)
 {
     pip_status st = check_args(d_vertices, num_vertices, d_poses, num_poses, d_points, num_points, tau,
                                d_workspace, workspace_bytes);
     if (st != PIP_OK) return st;
-    if (d_loss == nullptr) return PIP_E_INVALID_ARG;
+    if (d_loss == nullptr || (flags & ~PIP_PENALTY_CULL)) return PIP_E_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t tiles = num_points > 0 ? (num_points + kPenPoints - 1) / kPenPoints : 1;
     PenWorkspace w;
@@ -700,8 +818,12 @@ pip_status pip_penalty_forward(const float *d_vertices, int32_t num_vertices, co
     pen_begin_kernel<<<1, 32, 0, s>>>(w.voffs, w.worst, num_vertices);
     prepare_kernel<<<1, 32, 0, s>>>(d_vertices, PIP_F32, w.voffs, 1, num_vertices, w.g0, w.gk, w.coef,
                                     w.coefn, w.poly, w.worst);
-    launch_penalty<false>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses, d_points,
-                          num_points, tau);
+    if (flags & PIP_PENALTY_CULL)
+        launch_penalty<false, true>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses,
+                                    d_points, num_points, tau);
+    else
+        launch_penalty<false, false>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses,
+                                     d_points, num_points, tau);
     const int64_t blocks = tiles * num_poses;
     const int64_t g = (blocks + kRedPer - 1) / kRedPer;
     penalty_sum_kernel<<<(unsigned)g, kPenThreads, 0, s>>>(w.loss_part, blocks, kRedPer, w.loss_stage);
@@ -712,12 +834,13 @@ pip_status pip_penalty_forward(const float *d_vertices, int32_t num_vertices, co
 pip_status pip_penalty_backward(const float *d_vertices, int32_t num_vertices, const float *d_poses,
                                 int32_t num_poses, const float *d_points, int64_t num_points, float tau,
                                 const float *d_grad_loss, double *d_grad_vertices, double *d_grad_poses,
-                                void *d_workspace, size_t workspace_bytes, void *stream)
+                                int32_t flags, void *d_workspace, size_t workspace_bytes, void *stream)
 {
     pip_status st = check_args(d_vertices, num_vertices, d_poses, num_poses, d_points, num_points, tau,
                                d_workspace, workspace_bytes);
     if (st != PIP_OK) return st;
-    if (d_grad_vertices == nullptr || d_grad_poses == nullptr) return PIP_E_INVALID_ARG;
+    if (d_grad_vertices == nullptr || d_grad_poses == nullptr || (flags & ~PIP_PENALTY_CULL))
+        return PIP_E_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t tiles = num_points > 0 ? (num_points + kPenPoints - 1) / kPenPoints : 1;
     PenWorkspace w;
@@ -725,8 +848,12 @@ pip_status pip_penalty_backward(const float *d_vertices, int32_t num_vertices, c
     pen_begin_kernel<<<1, 32, 0, s>>>(w.voffs, w.worst, num_vertices);
     prepare_kernel<<<1, 32, 0, s>>>(d_vertices, PIP_F32, w.voffs, 1, num_vertices, w.g0, w.gk, w.coef,
                                     w.coefn, w.poly, w.worst);
-    launch_penalty<true>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses, d_points,
-                         num_points, tau);
+    if (flags & PIP_PENALTY_CULL)
+        launch_penalty<true, true>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses,
+                                   d_points, num_points, tau);
+    else
+        launch_penalty<true, false>(num_vertices, dim3((unsigned)tiles, (unsigned)num_poses), s, w, d_poses,
+                                    d_points, num_points, tau);
     const int64_t blocks = tiles * num_poses;
     // edge sums: kEdgeChunks slices per (edge, component); pose sums: one
     // block per (pose, component) over the pose's tiles

@@ -94,8 +94,8 @@ def test_host_argument_checks_of_the_other_entry_points(lib):
     # penalty: bad sizes and null pointers are refused; the workspace size grows with the blocks
     assert lib.pip_penalty_workspace_bytes(0, 1, 1) == 0
     assert lib.pip_penalty_workspace_bytes(12, 4, 1 << 20) > lib.pip_penalty_workspace_bytes(12, 4, 1 << 10) > 0
-    assert lib.pip_penalty_forward(None, 12, None, 4, None, 10, 0.05, None, None, 0, None) == B.PIP_E_INVALID_ARG
-    assert lib.pip_penalty_backward(None, 12, None, 4, None, 10, 0.05, None, None, None, None, 0,
+    assert lib.pip_penalty_forward(None, 12, None, 4, None, 10, 0.05, None, 0, None, 0, None) == B.PIP_E_INVALID_ARG
+    assert lib.pip_penalty_backward(None, 12, None, 4, None, 10, 0.05, None, None, None, 0, None, 0,
                                     None) == B.PIP_E_INVALID_ARG
     # the tuning cache can be set and cleared without a GPU
     assert lib.pip_set_tuning_cache(None) == B.PIP_OK

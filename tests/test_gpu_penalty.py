@@ -71,10 +71,11 @@ def _case(m=8192, poses=12, seed=40):
     return w.vertices, w.extra["poses"], w.points, w.extra["tau"]
 
 
-def test_penalty_loss_and_gradients_match_fp64_reference():
+@pytest.mark.parametrize("cull", [False, True])
+def test_penalty_loss_and_gradients_match_fp64_reference(cull):
     v, P, q, tau = _case()
-    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau).item()
-    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau, cull=cull).item()
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau, cull=cull)
     ref_loss, ref_gv, ref_gp = _oracle(v, P, q, tau)
     assert loss == pytest.approx(ref_loss, rel=1e-5)
     ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
@@ -83,14 +84,15 @@ def test_penalty_loss_and_gradients_match_fp64_reference():
     assert ok, "pose gradient: norm-wise %.2e, %s elements off" % (nrm, bad)
 
 
+@pytest.mark.parametrize("cull", [False, True])
 @pytest.mark.parametrize("n", [4, 7, 16, 20, 40])
-def test_penalty_other_edge_counts(n):
+def test_penalty_other_edge_counts(n, cull):
     """Register variants for up to 4, 8 and 16 edges and the shared-memory
-    variant above 16, each against the oracle."""
+    variant above 16, each against the oracle, with and without the cull."""
     w = wl.footprint_trajectory(seed=45 + n, m=6000, num_poses=7, n=n)
     v, P, q, tau = w.vertices, w.extra["poses"], w.points, w.extra["tau"]
-    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau).item()
-    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau, cull=cull).item()
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau, cull=cull)
     ref_loss, ref_gv, ref_gp = _oracle(v, P, q, tau)
     assert loss == pytest.approx(ref_loss, rel=1e-5)
     ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
@@ -123,13 +125,14 @@ def test_penalty_gradient_against_central_differences_of_fp64_loss():
             assert gp[j, d] == pytest.approx(fd, rel=1e-4, abs=1e-4 * np.abs(gp).max())
 
 
-def test_penalty_autograd_function():
+@pytest.mark.parametrize("cull", [False, True])
+def test_penalty_autograd_function(cull):
     v, P, q, tau = _case(m=4096, poses=6, seed=42)
     vt = _to(v).requires_grad_(True)
     pt = _to(P).requires_grad_(True)
-    loss = B.collision_penalty(vt, pt, _to(q), tau)
+    loss = B.collision_penalty(vt, pt, _to(q), tau, cull=cull)
     (3.0 * loss).backward()
-    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau, cull=cull)
     np.testing.assert_allclose(vt.grad.cpu().numpy(), 3.0 * gv.cpu().numpy(), rtol=1e-6, atol=1e-6)
     np.testing.assert_allclose(pt.grad.cpu().numpy(), 3.0 * gp.cpu().numpy(), rtol=1e-6, atol=1e-6)
 
@@ -144,13 +147,37 @@ def test_penalty_translation_invariance_on_gpu():
     assert l1 == pytest.approx(l0, rel=1e-5)
 
 
-def test_penalty_empty_points_and_invalid_footprint():
+@pytest.mark.parametrize("cull", [False, True])
+def test_penalty_empty_points_and_invalid_footprint(cull):
     v, P, q, tau = _case(m=16, poses=2, seed=44)
-    assert B.pip_penalty_forward(_to(v), _to(P), _to(q[:0]), tau).item() == 0.0
+    assert B.pip_penalty_forward(_to(v), _to(P), _to(q[:0]), tau, cull=cull).item() == 0.0
     bad = np.array([[0, 0], [2, 0], [1, 0.2], [2, 2], [0, 2]], np.float32)  # non-convex
-    assert B.pip_penalty_forward(_to(bad), _to(P), _to(q), tau).item() == 0.0
-    gv, gp = B.pip_penalty_backward(_to(bad), _to(P), _to(q), tau)
+    assert B.pip_penalty_forward(_to(bad), _to(P), _to(q), tau, cull=cull).item() == 0.0
+    gv, gp = B.pip_penalty_backward(_to(bad), _to(P), _to(q), tau, cull=cull)
     assert not gv.cpu().numpy().any() and not gp.cpu().numpy().any()
+
+
+def test_penalty_cull_of_points_all_far_away():
+    """Every point hundreds of tau beyond the footprint: every term and
+    gradient is exactly 0 in float32, with the cull (nothing kept) and
+    without; one point near a pose keeps the loss and gradient equal to the
+    full pass's and the oracle's."""
+    v, P, q, tau = _case(m=4000, poses=3, seed=46)
+    far = (q + np.float32(1000.0)).astype(np.float32)
+    for cull in (False, True):
+        assert B.pip_penalty_forward(_to(v), _to(P), _to(far), tau, cull=cull).item() == 0.0
+        gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(far), tau, cull=cull)
+        assert not gv.cpu().numpy().any() and not gp.cpu().numpy().any()
+    far[1234] = P[1, :2] + np.float32(0.5)
+    ref_loss, ref_gv, ref_gp = _oracle(v, P, far, tau)
+    for cull in (False, True):
+        loss = B.pip_penalty_forward(_to(v), _to(P), _to(far), tau, cull=cull).item()
+        gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(far), tau, cull=cull)
+        assert loss == pytest.approx(ref_loss, rel=1e-5)
+        ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
+        assert ok, "cull=%s vertex gradient: norm-wise %.2e, %s elements off" % (cull, nrm, bad)
+        ok, nrm, bad = _rel_ok(gp.cpu().numpy(), ref_gp)
+        assert ok, "cull=%s pose gradient: norm-wise %.2e, %s elements off" % (cull, nrm, bad)
 
 
 def test_penalty_full_size_every_gradient():
@@ -159,18 +186,20 @@ def test_penalty_full_size_every_gradient():
     against the oracle run over pose blocks on every host core."""
     w = wl.footprint_trajectory()
     v, P, q, tau = w.vertices, w.extra["poses"], w.points, w.extra["tau"]
-    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau).item()
-    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
     ref_loss, ref_gv, ref_gp = _oracle_threads(v, P, q, tau)
-    assert loss == pytest.approx(ref_loss, rel=1e-5)
-    ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
-    assert ok, "vertex gradient: norm-wise %.2e, %s of 24 elements off" % (nrm, bad)
-    ok, nrm, bad = _rel_ok(gp.cpu().numpy(), ref_gp)
-    assert ok, "pose gradient: norm-wise %.2e, %s of 768 elements off" % (nrm, bad)
+    for cull in (False, True):
+        loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau, cull=cull).item()
+        gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau, cull=cull)
+        assert loss == pytest.approx(ref_loss, rel=1e-5)
+        ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
+        assert ok, "cull=%s vertex gradient: norm-wise %.2e, %s of 24 elements off" % (cull, nrm, bad)
+        ok, nrm, bad = _rel_ok(gp.cpu().numpy(), ref_gp)
+        assert ok, "cull=%s pose gradient: norm-wise %.2e, %s of 768 elements off" % (cull, nrm, bad)
 
 
+@pytest.mark.parametrize("cull", [False, True])
 @pytest.mark.parametrize("n", [12, 20])
-def test_penalty_every_pair_near_the_footprint(n):
+def test_penalty_every_pair_near_the_footprint(n, cull):
     """Poses near the origin and points within 3 m of it: every (pose, point)
     pair has a nonzero gradient, so every warp's queue fills on every step
     (the benchmark's trajectory has ~6 % such pairs)."""
@@ -180,8 +209,8 @@ def test_penalty_every_pair_near_the_footprint(n):
                  axis=1).astype(np.float32)
     q = rng.uniform(-3.0, 3.0, size=(5003, 2)).astype(np.float32)
     v, tau = w.vertices, w.extra["tau"]
-    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau).item()
-    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau)
+    loss = B.pip_penalty_forward(_to(v), _to(P), _to(q), tau, cull=cull).item()
+    gv, gp = B.pip_penalty_backward(_to(v), _to(P), _to(q), tau, cull=cull)
     ref_loss, ref_gv, ref_gp = _oracle(v, P, q, tau)
     assert loss == pytest.approx(ref_loss, rel=1e-5)
     ok, nrm, bad = _rel_ok(gv.cpu().numpy(), ref_gv)
