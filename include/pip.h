@@ -129,8 +129,11 @@ pip_status pip_prepare_p0(const void *d_vertices, pip_dtype vdtype, const int32_
  *   mode              PIP_MASK and/or PIP_FIRST_HIT (first hit only when
  *                     d_point_offsets is NULL); PIP_CULL may be added for
  *                     the all-pairs test: a polygon is skipped for a warp's
- *                     points when none lies in its vertex bounding box, and
- *                     a block stops once each of its points has a candidate.
+ *                     points when none lies in its vertex bounding box and
+ *                     within its outer disc (see PIP_DISC), the points are
+ *                     decided inside without the edges when all of them lie
+ *                     in its inner disc, and a block stops once each of its
+ *                     points has a candidate.
  *                     Same results, less work; not the paper's full-work
  *                     timing convention (Sec. 6.2).  Ignored otherwise.
  *                     PIP_EARLY_EXIT may be added for one polygon or an

@@ -162,9 +162,12 @@ __device__ __forceinline__ float ap_s(const float4 &c, float x, float y)
 // CULL (pip_test's PIP_CULL): a warp skips a polygon when none of its points
 // that still lacks a candidate lies in the polygon's vertex bounding box (the
 // polygon lies inside that box exactly, and float32 rounding of a point is
-// monotone, so a skipped point is outside), and a CTA stops once every one of
-// its points has a candidate in its range (a later polygon cannot lower it).
-// Same keys for every point whose first hit lies in the range; fewer tests.
+// monotone, so a skipped point is outside) and within its outer disc (the
+// generator-radius cull: PolyInfo::tout, as in the disc filter); when every
+// such point lies inside the polygon's inner disc (PolyInfo::tin), they are
+// decided inside without the edges.  A CTA stops once every one of its points
+// has a candidate in its range (a later polygon cannot lower it).  Same first
+// hits for every point whose first hit lies in the range; fewer tests.
 template <bool INT, bool CULL>
 __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
     const PolyInfo *__restrict__ poly, const float4 *__restrict__ coefp, int P, const void *__restrict__ pts,
@@ -228,6 +231,28 @@ __global__ void __launch_bounds__(kApThreads, 2) allpairs_split_kernel(
                 for (int i = 0; i < kApPT; ++i)
                     open |= key[i] == 0xffffffffu && px[i] >= bx0 && px[i] <= bx1 && py[i] >= by0 && py[i] <= by1;
                 if (!__any_sync(0xffffffffu, open)) continue;
+                // the discs about o, with d2 of x = fl(p - o) as the edge loop forms it
+                bool in_disc[kApPT];
+                bool between = false;
+                open = false;
+#pragma unroll
+                for (int i = 0; i < kApPT; ++i) {
+                    const float xl = px[i] - pi.ox, yl = py[i] - pi.oy;
+                    const float d2 = fmaf(xl, xl, yl * yl);
+                    const bool cand = key[i] == 0xffffffffu && px[i] >= bx0 && px[i] <= bx1 && py[i] >= by0 &&
+                                      py[i] <= by1 && !(d2 > pi.tout);
+                    in_disc[i] = cand && d2 < pi.tin;
+                    open |= cand;
+                    between |= cand && !in_disc[i];
+                }
+                if (!__any_sync(0xffffffffu, open)) continue;
+                if (!__any_sync(0xffffffffu, between)) {
+                    const uint32_t jj = (uint32_t)(j0 + q) << 1;
+#pragma unroll
+                    for (int i = 0; i < kApPT; ++i)
+                        if (in_disc[i]) key[i] = jj;
+                    continue;
+                }
             }
             const float ox = pi.ox, oy = pi.oy;
             const int n = pi.n;  // at least 3
