@@ -276,7 +276,8 @@ pip_status pip_timing_read(pip_tables *t, int32_t *calls, double *bulk_ms, doubl
  * every variant `reps` times with CUDA events on the caller's own inputs
  * (synchronizes; not during capture), keeps the fastest in the tables and
  * returns it with its mean milliseconds.  pip_set_stream_variant picks one
- * directly (for a cached tuning result).
+ * directly (for a cached tuning result).  The disc filter (PIP_DISC) runs at
+ * the chosen shape as well.
  */
 int32_t pip_stream_variant_count(void);
 pip_status pip_set_stream_variant(pip_tables *t, int32_t variant);

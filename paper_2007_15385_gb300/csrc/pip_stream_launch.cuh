@@ -14,11 +14,17 @@ using namespace pip;
 
 
 // Variants of the pipelined kernel: (points per lane per stage, stages).
+// Since a consumer warp hands its stage back once the points are in
+// registers, fewer and larger stages (bigger bulk copies) pay.
 struct StreamVariant {
     int ppl, stages;
 };
-constexpr StreamVariant kStreamVariants[] = {{16, 3}, {16, 2}, {8, 4}, {8, 6}};
+constexpr StreamVariant kStreamVariants[] = {{16, 3}, {16, 2}, {24, 2}, {20, 2}};
 constexpr int kNumStreamVariants = sizeof(kStreamVariants) / sizeof(kStreamVariants[0]);
+// the refine queue's slack (pip_prepare) holds one tile per CTA at two CTAs a SM
+static_assert(StreamCfg<24, 2>::kTile <= kMaxStreamTile && StreamCfg<20, 2>::kTile <= kMaxStreamTile &&
+                  StreamCfg<16, 3>::kTile <= kMaxStreamTile,
+              "a stream tile larger than the refine queue's slack");
 
 template <int NE, int PPL, int STAGES, bool INT, bool EARLY = false, bool DISC = false>
 cudaError_t launch_tma_one(const pip_tables *t, const void *pts, int64_t M, uint32_t *mask, cudaStream_t s)
@@ -93,8 +99,8 @@ cudaError_t launch_stream_tma(const pip_tables *t, const void *pts, int64_t M, u
 {
     switch (t->stream_variant) {
     case 1: return launch_tma_ne<16, 2, INT, false, DISC>(t, pts, M, mask, s);
-    case 2: return launch_tma_ne<8, 4, INT, false, DISC>(t, pts, M, mask, s);
-    case 3: return launch_tma_ne<8, 6, INT, false, DISC>(t, pts, M, mask, s);
+    case 2: return launch_tma_ne<24, 2, INT, false, DISC>(t, pts, M, mask, s);
+    case 3: return launch_tma_ne<20, 2, INT, false, DISC>(t, pts, M, mask, s);
     default: return launch_tma_ne<16, 3, INT, false, DISC>(t, pts, M, mask, s);
     }
 }
@@ -106,12 +112,12 @@ cudaError_t set_all_attr()
     // the disc filter's forms of the four tile shapes
     if (e == cudaSuccess) e = set_smem_attr<16, 3, INT, false, true>();
     if (e == cudaSuccess) e = set_smem_attr<16, 2, INT, false, true>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 4, INT, false, true>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 6, INT, false, true>();
+    if (e == cudaSuccess) e = set_smem_attr<24, 2, INT, false, true>();
+    if (e == cudaSuccess) e = set_smem_attr<20, 2, INT, false, true>();
     if (e == cudaSuccess) e = set_smem_attr<16, 3, INT>();
     if (e == cudaSuccess) e = set_smem_attr<16, 2, INT>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 4, INT>();
-    if (e == cudaSuccess) e = set_smem_attr<8, 6, INT>();
+    if (e == cudaSuccess) e = set_smem_attr<24, 2, INT>();
+    if (e == cudaSuccess) e = set_smem_attr<20, 2, INT>();
     return e;
 }
 
