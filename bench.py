@@ -47,8 +47,8 @@ FALLBACK_HBM_GBS = 6800.0
 # workload, from one ncu capture of 2^25 points scaled by 2 to the 2^26-point
 # launch, valid only while the kernel sources hash to the value recorded with it.
 # keyed by the tile variant the autotuner picks (2: 24 points per lane x 2
-# stages, 3: 20 x 2)
-NCU_TRAFFIC = {"bytes_by_variant": {2: 548049920, 3: 548409856}, "sources_sha": "bcf24e3333b7b30d"}
+# stages, 3: 20 x 2, 4: 24 x 2 at 16 consumer warps)
+NCU_TRAFFIC = {"bytes_by_variant": {2: 548285440, 3: 548588032, 4: 548974592}, "sources_sha": "15dc8a5832480fdb"}
 # GB300 HBM3e nominal bandwidth, reported beside the measured-peak fraction
 NOMINAL_HBM_GBS = 7900.0
 KERNEL_SOURCES = ["paper_2007_15385_gb300/csrc/pip_stream_tma.cuh",

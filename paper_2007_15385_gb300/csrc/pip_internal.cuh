@@ -25,10 +25,10 @@ constexpr int kMaxEdges = 64;
 constexpr int kMinEdges = 3;
 // Row stride of the padded coefficient table: 64 edges rounded up, plus room.
 constexpr int kPadStride = kMaxEdges + 4;
-// the largest tile (points per stage) of the pipelined single-polygon kernel:
-// 8 consumer warps x 32 lanes x 24 points; the refine queue keeps one such
-// tile of slack per CTA
-constexpr int kMaxStreamTile = 8 * 32 * 24;
+// the refine queue's slack for the pipelined single-polygon kernel, in points
+// a SM: one tile per CTA, e.g. two CTAs of 8 consumer warps x 32 lanes x 24
+// points, or one of 16 warps
+constexpr int kStreamSlackPerSm = 2 * 8 * 32 * 24;
 // Integer vertices must satisfy |v| <= 2^24 so that float32 holds them exactly
 // and every exact cross product fits in int64.
 constexpr int32_t kIntLimit = 1 << 24;

@@ -181,7 +181,7 @@ static pip_status prepare_impl(const void *d_vertices, pip_dtype vdtype, const i
     const size_t o_cnt = take(128);
     // refine queue: every point once, plus the slack of the pipelined kernel's
     // per-CTA slices (at most one tile of 4,096 points per CTA, 2 CTAs per SM)
-    const size_t queue_entries = (size_t)max_points + (size_t)(2 * t->num_sms + 1) * kMaxStreamTile;
+    const size_t queue_entries = (size_t)max_points + (size_t)(t->num_sms + 1) * kStreamSlackPerSm;
     const size_t o_queue = take(queue_entries * sizeof(uint32_t));
     // all-pairs candidate keys (also used by one polygon when a first hit is asked for)
     const size_t o_keys = take((size_t)(max_points > 0 ? max_points : 1) * sizeof(uint32_t));

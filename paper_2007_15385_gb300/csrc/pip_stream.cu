@@ -18,7 +18,7 @@ cudaError_t launch_cmp_one(const pip_tables *t, const float *pts, int64_t M, uin
     using C = StreamCfg<kCmpPPL, kCmpStages>;
     auto k = stream_tma_kernel<NE, kCmpPPL, kCmpStages, false, OP>;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStreamThreads, C::kSmem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::kThreads, C::kSmem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     if (per_sm > 2) per_sm = 2;
@@ -45,7 +45,7 @@ cudaError_t launch_cmp_one(const pip_tables *t, const float *pts, int64_t M, uin
         sp.y1[e] = y.y;
     }
     const float4 *rows = OP == kTmaSign ? t->d_cmp_sign : t->d_cmp_ray;
-    k<<<blocks, kStreamThreads, C::kSmem, s>>>(sp, t->d_poly, rows, t->d_g0, t->d_gk, t->d_verts, t->vdtype, pts,
+    k<<<blocks, C::kThreads, C::kSmem, s>>>(sp, t->d_poly, rows, t->d_g0, t->d_gk, t->d_verts, t->vdtype, pts,
                                                M, mask, t->d_queue, (StreamCounters *)t->d_stream_ctr, t->d_qcount,
                                                t->d_error);
     return cudaGetLastError();

@@ -4,7 +4,9 @@
 // Persistent CTAs: one producer warp streams tiles of points from HBM into a
 // ring of shared-memory stages with 1-D bulk copies (cp.async.bulk), each
 // stage guarded by a "full" mbarrier (transaction bytes) and an "empty"
-// mbarrier (one arrive per consumer warp).  Consumer warps evaluate the
+// mbarrier (one arrive per consumer warp, made as soon as the warp's points
+// are in registers, so that the producer refills the stage during the edge
+// math).  Consumer warps (8, or 16 in one CTA a SM) evaluate the
 // expanded Eq. 11, s_k = t_k - x w_kx - y w_ky, with two FMAs per edge and
 // take the "for all k" of Alg. 5 as a NaN-propagating running min; for up to
 // 16 edges the coefficients sit in registers (edge count a template
@@ -28,23 +30,26 @@ struct StreamCounters {
     unsigned int ticket;
 };
 
+// consumer warps of a CTA: 8 (two CTAs a SM), or 16 (one CTA a SM, stages of
+// twice the size at the same shared memory per SM)
 constexpr int kConsumerWarps = 8;
-constexpr int kStreamThreads = (kConsumerWarps + 1) * 32;
 
 // DISC: each consumer warp also owns PPL mask words in shared memory (the
 // disc filter's inside bits of the points it sends through the full test).
-template <int PPL, int STAGES, bool DISC = false>
+// CW: consumer warps.
+template <int PPL, int STAGES, bool DISC = false, int CW = kConsumerWarps>
 struct StreamCfg {
-    static constexpr int kTile = kConsumerWarps * 32 * PPL;  // points per stage
+    static constexpr int kThreads = (CW + 1) * 32;  // the consumers and one producer warp
+    static constexpr int kTile = CW * 32 * PPL;  // points per stage
     static constexpr size_t kStageBytes = (size_t)kTile * 8;
     static constexpr size_t kCoefOff = STAGES * kStageBytes;
     static constexpr int kCoef = 2 * (kMaxEdges + 4);  // float4 (w_x, w_y, t, 0), padded to 4; ray: two per edge
     static constexpr size_t kBarOff = kCoefOff + (size_t)kCoef * 16;
     static constexpr size_t kDiscOff = kBarOff + 2 * STAGES * sizeof(uint64_t);
     static constexpr size_t kDiscWarpBytes = (size_t)PPL * 4;
-    static constexpr size_t kSmem = kDiscOff + (DISC ? kConsumerWarps * kDiscWarpBytes : 0);
-    // two CTAs per SM (16 consumer warps, <= 112 registers a thread) when the
-    // shared memory allows it
+    static constexpr size_t kSmem = kDiscOff + (DISC ? CW * kDiscWarpBytes : 0);
+    // two CTAs per SM (<= 112 registers a thread at 8 consumer warps) when
+    // the shared memory allows it
     static constexpr int kFit = (int)((227 * 1024) / (kSmem + 1024));
     static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > 2 ? 2 : kFit);
 };
@@ -498,15 +503,18 @@ __device__ __forceinline__ void consume_slice_cmp(const SliceCtx &cx, const unsi
 // OP: the Voronoi test (with its exact refine) or a comparator (no refine;
 // `coef` is then the polygon's comparator row, padded with NaN).
 // DISC: the disc filter of consume_slice_disc (the Voronoi test only).
-template <int NE, int PPL, int STAGES, bool INT, int OP = kTmaVoronoi, bool EARLY = false, bool DISC = false>
-__global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES, DISC>::kMinBlocks) stream_tma_kernel(
+// CW: consumer warps of the CTA.
+template <int NE, int PPL, int STAGES, bool INT, int OP = kTmaVoronoi, bool EARLY = false, bool DISC = false,
+          int CW = kConsumerWarps>
+__global__ void __launch_bounds__(StreamCfg<PPL, STAGES, DISC, CW>::kThreads,
+                                  StreamCfg<PPL, STAGES, DISC, CW>::kMinBlocks) stream_tma_kernel(
     const __grid_constant__ StreamPoly sp, const PolyInfo *__restrict__ poly, const float4 *__restrict__ coef,
     const double2 *__restrict__ g0tab, const double2 *__restrict__ gktab,
     const void *__restrict__ verts, int vdtype, const void *__restrict__ pts, int64_t M,
     uint32_t *__restrict__ mask, uint32_t *__restrict__ queue, StreamCounters *__restrict__ ctr,
     unsigned int *__restrict__ last_refine, int *__restrict__ err)
 {
-    using C = StreamCfg<PPL, STAGES, DISC>;
+    using C = StreamCfg<PPL, STAGES, DISC, CW>;
     constexpr int kTile = C::kTile;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *cs = (float4 *)(smem + C::kCoefOff);
@@ -534,7 +542,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES, DISC>::
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
+            mbar_init(&empty[s], CW);
         }
         s_refined = 0;
         fence_mbar_init();
@@ -547,7 +555,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES, DISC>::
     const int64_t per_cta = ((ntiles + gridDim.x - 1) / gridDim.x) * kTile;
     uint32_t *myqueue = queue + (int64_t)blockIdx.x * per_cta;
 
-    if (warp == kConsumerWarps) {
+    if (warp == CW) {
         // ---------------- producer: one elected lane issues the bulk copies
         if (lane == 0) {
             const int nmine = (int)mine;
@@ -641,7 +649,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<PPL, STAGES, DISC>::
     // warp of the CTA, the producer's included); their mask words were
     // written above with the bit clear
     const unsigned int nq = s_refined;
-    for (unsigned int i = warp; i < nq; i += kConsumerWarps + 1) {
+    for (unsigned int i = warp; i < nq; i += CW + 1) {
         const int64_t p = myqueue[i];
         if (warp_inside_exact(poly, 0, g0tab, gktab, verts, vdtype, pts, INT ? PIP_I32 : PIP_F32, p) &&
             lane == 0)
